@@ -1,0 +1,358 @@
+"""Benchmark: masked-LDDMM gradient-descent iterations per second at 264x160x228, T = 10.
+
+One step = one full iteration of the hot path on one GPU: backward flow sweep, forward flow
+sweep with the masked residual, K = (gamma - alpha Lap)^-2 per time step, the update and the
+FP64 energy reductions (all T = 10 time steps).  Inputs: the brain-shaped synthetic atlas/target
+mask pair at 264x160x228 (seeded), resident in HBM before the timed region; the working set
+(~3 GB: v, per-time-step J1/W, maps, spectra) is far larger than L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun): N independent replicas, one per GPU (registrations do not exchange data);
+value = iterations of all ranks / max-over-ranks time.  --impl reference times the FP64 CPU
+oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SHAPE = (228, 160, 264)            # (Z, Y, X): 264 x 160 x 228 voxels, 50 um box
+BASE = (114, 80, 132)              # generator scale: the 100 um grid
+T = 10
+METRIC = "LDDMM iters/s at 264x160x228 T=10"
+UNIT = "iter/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1605_02060_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        with open(os.path.join(d, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+# Algorithmic bytes (or flops) per voxel for one launch of each kernel (fp32 storage);
+# the derivation is in the design notes: each field is read or written once per launch.
+def algorithmic(kernel, N, dims, kmode):
+    X, Y, Z = dims
+    B = {"flow_back_disp": 36, "flow_back_terms": 28, "fwd_residual": 36,
+         "fwd_flow_ereg": 36, "update": 36}
+    if kernel in B:
+        return {"bound": "hbm", "bytes": B[kernel] * N}
+    L = {"K_x_fwd": X, "K_x_inv_update": X, "K_y_fwd": Y, "K_y_inv": Y, "K_z_symbol": Z,
+         "K_z_inv": Z}[kernel]
+    flops = 2.0 * L * 3 * N          # dense real DFT along one axis, 3 components
+    return {"bound": "alu" if kmode == 0 else "tensor", "flops": flops, "bytes": 24 * N}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [l.strip().split(",") for l in self.out.read().splitlines() if l.strip()]
+        os.unlink(self.out.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, val in zip(names, r[5:9]):
+                    if val.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_inputs(seed=1):
+    from paper_1605_02060_gb300 import synth
+    pair, _ = synth.brain_pair(shape=SHAPE, base_shape=BASE, seed=seed)
+    return pair
+
+
+def oracle_sample_rate(pair, frac_z, frac_y=1.0, frac_x=1.0):
+    """Time one T=1 iteration of the FP64 oracle on the central crop of the workload and scale
+    to iterations/s of the full T=10 workload (work is linear in voxels and in T)."""
+    import numpy as np
+
+    from oracle import lddmm as O
+    Z, Y, X = SHAPE
+    cz, cy, cx = int(round(Z * frac_z)), int(round(Y * frac_y)), int(round(X * frac_x))
+    z0, y0, x0 = (Z - cz) // 2, (Y - cy) // 2, (X - cx) // 2
+    sl = (slice(z0, z0 + cz), slice(y0, y0 + cy), slice(x0, x0 + cx))
+    I0, I1, M = pair.I0[sl], pair.I1[sl], pair.M[sl]
+    v = np.zeros((1, 3) + I0.shape)
+    t0 = time.perf_counter()
+    O.lddmm_step(v, I0, I1, M, O.Params(T=1))
+    dt = time.perf_counter() - t0
+    scale = (Z * Y * X) / float(cz * cy * cx) * T
+    return 1.0 / (dt * scale), dt, "%dx%dx%d crop, T=1 (1/%.0f of one iteration)" % (cx, cy, cz, scale)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    pair = make_inputs()
+    rates = []
+    for i in range(args.warmup + args.steps):
+        r, dt, sample = oracle_sample_rate(pair, 0.5, 0.5, 0.5)
+        if i >= args.warmup:
+            rates.append(r)
+    value = statistics.mean(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "masked LDDMM 264x160x228 T=10, brain-shaped "
+                                             "atlas/target mask pair (seed 1)", "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample + " per step; NumPy/SciPy FP64, one thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1605_02060_gb300 import lddmm as L
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    L.load()
+    pair = make_inputs()
+    Z, Y, X = SHAPE
+    N = X * Y * Z
+    dev = torch.device("cuda", local)
+    I0 = torch.from_numpy(pair.I0).to(dev)
+    I1 = torch.from_numpy(pair.I1).to(dev)
+    M = torch.from_numpy(pair.M).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    p = L.default_params(X, Y, Z, T=T, k_mode=args.kmode)
+    ctx = L.Lddmm(p, I0, I1, M, stream=stream)
+    # warm-up
+    for _ in range(args.warmup):
+        ctx.step(want_energy=False)
+    torch.cuda.synchronize()
+    # timed region
+    launches_per_step = T * 11 + 8
+    ctx.profile_start(launches_per_step * args.steps + 64)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ctx.step(want_energy=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_stop()
+    ms_max = max_over_ranks(ws, ms)
+    value = ws * args.steps / (ms_max / 1000.0)
+    e_last = ctx.energy()
+    # end to end through the public API with host buffers: every step copies the images in from
+    # pinned host memory and reads the energy back
+    h0 = torch.from_numpy(pair.I0).pin_memory()
+    h1 = torch.from_numpy(pair.I1).pin_memory()
+    hm = torch.from_numpy(pair.M).pin_memory()
+    e2e_steps = max(1, min(args.steps, 10))
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.set_images(h0, h1, hm)
+        ctx.step(want_energy=True)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(ws, time.perf_counter() - t0)
+    e2e = {"value": ws * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 3 * N * 4,
+           "d2h_bytes_per_step": ctypes_sizeof_energy()}
+    ctx.close()
+    if rank != 0:
+        return 0
+    # roofline of the dominant kernel
+    peaks, src = _peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (nl, tot_ms) = dom
+    avg_s = tot_ms / nl / 1000.0
+    alg = algorithmic(name, N, (X, Y, Z), args.kmode)
+    traffic = _traffic(name)
+    if alg["bound"] == "hbm":
+        achieved = alg["bytes"] / avg_s / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": name,
+                "peak_source": src + " (copy bandwidth)"}
+    elif alg["bound"] == "tensor":
+        achieved = alg["flops"] / avg_s / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": name,
+                "peak_source": src + " (bf16 sustained)"}
+    else:
+        sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x clock
+        achieved = alg["flops"] / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": name,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz}
+    # CPU baseline: the oracle, one thread, on half the grid at T=1
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        r, dt, sample = oracle_sample_rate(pair, 0.5)
+        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": sample + "; NumPy/SciPy FP64, one thread; %.1f s" % dt}
+    kname = {0: "fp32", 1: "bf16x3", 2: "bf16"}[args.kmode]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "masked LDDMM 264x160x228 T=10, brain-shaped atlas/target mask "
+                                   "pair (seed 1), fp32 fields, K via %s DFT products" % kname,
+                       "grid": [X, Y, Z], "T": T, "alpha": 0.02, "gamma": 1.0, "sigma": 0.1,
+                       "epsilon": 1e-3, "k_mode": kname,
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "working set %.1f GB > L2 (no flush)" % (
+                           (2 * T * 3 + 2 * T + 20) * N * 4 / 1e9)},
+            "clocks": clk, "e2e": e2e, "gpu_launches": int(sum(v[0] for v in prof.values())),
+            "roofline": roof, "cpu_baseline": cpu,
+            "kernels": {k: {"launches": v[0], "ms": round(v[1], 3),
+                            "share": round(v[1] / sum(x[1] for x in prof.values()), 4)}
+                        for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+            "energy_after": e_last["total"]}
+    print(json.dumps(line))
+    return 0
+
+
+def ctypes_sizeof_energy():
+    import ctypes
+
+    from paper_1605_02060_gb300 import lddmm as L
+    return ctypes.sizeof(L.lddmm_energy)
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the
+    current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("csrc_hash") != _csrc_hash():
+        return None
+    e = d.get("kernels", {}).get(kernel)
+    return None if e is None else e.get("dram_bytes_per_launch")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--kmode", type=int, default=None, help="0 fp32, 1 bf16x3, 2 bf16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.kmode is None:
+        args.kmode = DEFAULT_KMODE
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+DEFAULT_KMODE = 0
+
+if __name__ == "__main__":
+    sys.exit(main())

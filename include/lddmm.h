@@ -1,0 +1,171 @@
+/*
+ * liblddmm — masked LDDMM registration of 3D volumes on one GB300 GPU (sm_103a).
+ *
+ * Method: Kutten et al., "Deformably registering and annotating whole CLARITY brains to an
+ * atlas via masked LDDMM" (SPIE 2016).  §2.4 defines the energy
+ *     E(v) = int_0^1 ||L v_t||^2 dt + sigma^-2 ||J0 o phi_10 - J1||^2,  L = (-alpha Lap + gamma) I3,
+ * minimised by gradient descent over a time-varying velocity field v; §2.3 (Mask-LDDMM) passes
+ * the brain masks as the images; §2.5 pulls the atlas labels back through phi_10.  The gradient
+ * and the update are those of Beg et al. 2005 (cited in §2.4):
+ *     v_t <- v_t - eps (2 v_t - K[(2/sigma^2) (M o phi_t1) |D phi_t1| (J0_t - J1_t) grad J0_t]),
+ *     K = (gamma - alpha Lap_h)^-2 on the periodic grid.
+ *
+ * Discretisation used by every entry point (the paper gives only the continuous method):
+ *   - grid nx x ny x nz, C order [z][y][x] (x fastest), spacing (hx, hy, hz);
+ *   - T time steps, dt = 1/T; velocity v laid out [T][3][nz][ny][nx] float32, components (x,y,z),
+ *     in physical units (voxel spacing units per unit time);
+ *   - first-order semi-Lagrangian flows, one trilinear lookup per step:
+ *       phi_{j,1}(x) = phi_{j+1,1}(x + dt v_j(x)),  phi_{j+1,0}(x) = phi_{j,0}(x - dt v_j(x));
+ *   - maps are returned as displacements u = phi - id, [3][nz][ny][nx] float32, in voxels;
+ *   - trilinear interpolation with clamp-to-edge coordinates; gradients and D phi by central
+ *     differences inside, one-sided at the faces; Lap_h the periodic 7-point Laplacian;
+ *   - E = hx hy hz [dt sum_j sum_x |(gamma - alpha Lap_h) v_j|^2
+ *                   + sigma^-2 sum_x M (I0 o phi_10 - I1)^2].
+ *
+ * Memory: every pointer argument may address device memory or host memory (pinned or
+ * pageable): data moves with cudaMemcpyAsync(cudaMemcpyDefault) on the context's stream.  The
+ * caller owns every pointer it passes; the library copies inputs in and writes only the
+ * destination buffers it is given.  The context owns its device buffers until lddmm_destroy.
+ * Work is enqueued on the context's stream; a call that returns scalars or writes host memory
+ * waits for that stream (bounded wait: LDDMM_ERR_TIMEOUT after params.timeout_s seconds).
+ * Errors: a negative status; lddmm_last_error() describes the last failure of that context.
+ * No exception crosses this interface.  After LDDMM_ERR_CUDA the context must be destroyed;
+ * after any other error it stays usable.  One context may be used by one host thread at a time.
+ */
+#ifndef LDDMM_H
+#define LDDMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lddmm_ctx lddmm_ctx;
+
+enum {
+  LDDMM_OK = 0,
+  LDDMM_ERR_INVALID_ARG = -1,
+  LDDMM_ERR_OOM = -2,
+  LDDMM_ERR_CUDA = -3,
+  LDDMM_ERR_NONFINITE = -4,
+  LDDMM_ERR_STATE = -5,
+  LDDMM_ERR_TIMEOUT = -6
+};
+
+/* How K is applied (per-axis real DFTs written as dense matrix products). */
+enum {
+  LDDMM_K_FP32 = 0,    /* FP32 products on the CUDA cores (reference form)            */
+  LDDMM_K_BF16X3 = 1,  /* tensor cores, split bf16 x3 products, FP32 accumulation      */
+  LDDMM_K_BF16 = 2     /* tensor cores, plain bf16 products, FP32 accumulation         */
+};
+
+/* What lddmm_get_field returns. */
+enum {
+  LDDMM_FIELD_U10 = 0, /* phi_{1,0} - id, [3][nz][ny][nx] voxels (template -> target pull-back) */
+  LDDMM_FIELD_U01 = 1, /* phi_{0,1} - id, [3][nz][ny][nx] voxels                                */
+  LDDMM_FIELD_J0 = 2,  /* deformed template I0 o phi_{1,0}, [nz][ny][nx]                         */
+  LDDMM_FIELD_I0 = 3,  /* template at the current level                                          */
+  LDDMM_FIELD_I1 = 4,  /* target at the current level                                            */
+  LDDMM_FIELD_M = 5    /* weight mask at the current level                                       */
+};
+
+/* Problem parameters (§2.4: alpha, gamma, sigma; time steps; gradient-descent step). */
+typedef struct {
+  int nx, ny, nz;            /* finest grid (each >= 2 at every level)                      */
+  float hx, hy, hz;          /* finest voxel spacing (> 0)                                   */
+  int T;                     /* time steps (>= 1)                                            */
+  float alpha, gamma, sigma; /* L = (-alpha Lap + gamma), sigma of the data term (> 0)       */
+  float epsilon;             /* gradient-descent step size (> 0)                             */
+  int iterations;            /* iterations per level for lddmm_register (>= 0)               */
+  int num_levels;            /* 1..4                                                         */
+  int level_factor[4];       /* coarse -> fine downsampling factors, last must be 1, e.g. 4,2,1 */
+  int k_mode;                /* LDDMM_K_*                                                    */
+  int flags;                 /* bit 0: halve epsilon and retry when the energy increases     */
+  float timeout_s;           /* bound on every host wait for the stream (<= 0: 600 s)        */
+} lddmm_params;
+
+/* Energy of the velocity field at the start of an iteration (§2.4), FP64 reductions. */
+typedef struct {
+  double total, reg, data;   /* E = reg + data                                              */
+  double min_det;            /* min over j, x of det D phi_{j,1} (fold check: <= 0 folds)    */
+  int iter, level, fold;     /* iteration index, level index, 1 if min_det <= 0              */
+  int pad;
+} lddmm_energy;
+
+/* Fill p with the defaults used by the tests: h = 1, T = 10, alpha = 0.02, gamma = 1,
+ * sigma = 0.1, eps = 1e-3, 20 iterations, one level, K on the tensor cores (bf16x3). */
+int lddmm_default_params(lddmm_params* p, int nx, int ny, int nz);
+
+/* Create a context: validates p, allocates device buffers for all levels, copies I0
+ * (template), I1 (target) and M (weight mask, NULL = all ones; each nx*ny*nz float32) in,
+ * builds the image pyramid and sets v = 0 at the coarsest level.  stream = cudaStream_t or NULL
+ * (a private stream is created).  Returns LDDMM_ERR_NONFINITE if an input holds NaN/Inf. */
+int lddmm_create(const lddmm_params* p, const float* I0, const float* I1, const float* M,
+                 void* stream, lddmm_ctx** out);
+
+/* Replace the images at the finest level (and rebuild the pyramid), keeping v. */
+int lddmm_set_images(lddmm_ctx* ctx, const float* I0, const float* I1, const float* M);
+
+/* One gradient-descent iteration at the current level (Beg update).  out = NULL: fully
+ * asynchronous; otherwise waits and fills *out with the energy of v before the update. */
+int lddmm_step(lddmm_ctx* ctx, lddmm_energy* out);
+
+/* Full schedule: for each remaining level, `iterations` steps, then upsample v to the next
+ * level.  trace (NULL or room for num_levels*iterations entries) receives every energy. */
+int lddmm_register(lddmm_ctx* ctx, lddmm_energy* trace, int trace_len);
+
+/* Move to level `level` (0 = coarsest), carrying v over by trilinear resampling. */
+int lddmm_set_level(lddmm_ctx* ctx, int level);
+/* Grid of the current level. */
+int lddmm_grid(lddmm_ctx* ctx, int* nx, int* ny, int* nz, int* level);
+
+/* dst = src o phi_{1,0} (direction 0, template into target space) or src o phi_{0,1}
+ * (direction 1), trilinear, on the current level grid (§2.4, §2.7). */
+int lddmm_warp(lddmm_ctx* ctx, const float* src, float* dst, int direction);
+
+/* dst = L0 o phi_{1,0} by nearest neighbour: index floor(x + u + 0.5) per axis in float32,
+ * clamped to the grid (§2.5).  uint16 labels, nx*ny*nz each, current level grid. */
+int lddmm_transfer_labels(lddmm_ctx* ctx, const uint16_t* L0, uint16_t* dst);
+
+/* Velocity field of the current level, [T][3][nz][ny][nx] float32. */
+int lddmm_get_velocity(lddmm_ctx* ctx, float* dst);
+int lddmm_set_velocity(lddmm_ctx* ctx, const float* src);
+
+/* One of LDDMM_FIELD_*, for the current v (flows are recomputed if v changed). */
+int lddmm_get_field(lddmm_ctx* ctx, int which, float* dst);
+
+/* dst = K src for one scalar field on the current level grid, using params.k_mode. */
+int lddmm_apply_K(lddmm_ctx* ctx, const float* src, float* dst);
+
+/* Energy of the current v without updating it. */
+int lddmm_energy_eval(lddmm_ctx* ctx, lddmm_energy* out);
+
+/* Mean Dice overlap over labels > 0 present in A or B (uint16, n voxels each). */
+int lddmm_dice(lddmm_ctx* ctx, const uint16_t* A, const uint16_t* B, int64_t n, double* out);
+
+/* Per-kernel device time, summed over the launches since lddmm_profile_start. */
+typedef struct {
+  char name[32];
+  int launches;
+  int pad;
+  double total_ms;
+} lddmm_kernel_stat;
+
+/* Record a pair of CUDA events on the context stream around each of the next max_launches
+ * kernel launches of lddmm_step (timing only; the computation is unchanged). */
+int lddmm_profile_start(lddmm_ctx* ctx, int max_launches);
+/* Stop recording, wait for the stream and sum device time per kernel into out[0..max_out);
+ * *n_out = number of distinct kernels seen.  LDDMM_ERR_STATE if max_launches was too small. */
+int lddmm_profile_stop(lddmm_ctx* ctx, lddmm_kernel_stat* out, int max_out, int* n_out);
+
+/* Change the bound on host waits for this context (seconds, <= 0: 600 s). */
+int lddmm_set_timeout(lddmm_ctx* ctx, float seconds);
+
+const char* lddmm_last_error(lddmm_ctx* ctx);
+void lddmm_destroy(lddmm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LDDMM_H */

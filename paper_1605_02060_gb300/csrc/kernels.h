@@ -1,0 +1,88 @@
+// Host-side launch wrappers for the liblddmm kernels (one translation unit per kernel family).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace lddmm {
+
+// Accumulators written by the reduction kernels (device memory, reset per iteration).
+struct Acc {
+  double e_reg;       // sum_j sum_x |(gamma - alpha Lap_h) v_j|^2   (unscaled)
+  double e_data;      // sum_x M (J0_T - I1)^2                       (unscaled)
+  int min_det_ord;    // ordered-int encoding of min det D phi_{j,1}
+  int nonfinite;      // set when a reduction saw NaN/Inf
+};
+
+// Optional timing hook: mark(user, kernel_id, 0) before and mark(user, kernel_id, 1) after
+// every kernel launch (the host records CUDA events on the launching stream).
+struct Hook {
+  void (*mark)(void* user, int kernel_id, int phase) = nullptr;
+  void* user = nullptr;
+  void operator()(int id, int phase) const {
+    if (mark) mark(user, id, phase);
+  }
+};
+
+enum KernelId {
+  KID_BACK_DISP = 0, KID_BACK_TERMS, KID_FWD_TERMS, KID_FWD_FLOW, KID_KX_FWD, KID_KY_FWD,
+  KID_KZ_SYM, KID_KZ_INV, KID_KY_INV, KID_KX_INV, KID_UPDATE, KID_COUNT
+};
+
+// ---- flows (kernels_flow.cu) ----
+// Backward sweep step j: u_cur = dt v_j / h + u_next(x + dt v_j / h)  (u_next == nullptr: id),
+// then J1_j = I1 o phi, W_j = (M o phi) det(I + Du_cur), min det into acc.
+void launch_flow_back(const Grid& g, const float* vj, const float* u_next, float* u_cur,
+                      const float* I1, const float* M, float* J1j, float* Wj, float dtx,
+                      float dty, float dtz, Acc* acc, cudaStream_t s, const Hook& hook);
+// Forward sweep step j: b = c W_j (J0_j - J1_j) grad J0_j / h,  J0_j = I0 o (id + u_cur).
+void launch_fwd_terms(const Grid& g, const float* u_cur, const float* I0, const float* J1j,
+                      const float* Wj, float* b, float c, float ihx, float ihy, float ihz,
+                      cudaStream_t s);
+// Forward sweep step j: u_next = -dt v_j / h + u_cur(x - dt v_j / h) (u_cur == nullptr: id),
+// E_reg contribution of v_j; if last, J0_T = I0 o (id + u_next) and E_data.
+void launch_fwd_flow(const Grid& g, const float* vj, const float* u_cur, float* u_next,
+                     float dtx, float dty, float dtz, float alpha, float gamma, float ihx2,
+                     float ihy2, float ihz2, bool last, const float* I0, const float* I1,
+                     const float* M, float* J0T, Acc* acc, cudaStream_t s);
+// v_j <- v_j - eps (2 v_j - Kb), 3 components.
+void launch_update(const Grid& g, float* vj, const float* Kb, float eps, cudaStream_t s);
+// Displacement of phi_{1,0} only (flows without the residual), used to refresh maps.
+void launch_flow_only_fwd(const Grid& g, const float* vj, const float* u_cur, float* u_next,
+                          float dtx, float dty, float dtz, cudaStream_t s);
+void launch_flow_only_back(const Grid& g, const float* vj, const float* u_next, float* u_cur,
+                           float dtx, float dty, float dtz, cudaStream_t s);
+void launch_warp(const Grid& g, const float* src, const float* u, float* dst, cudaStream_t s);
+void launch_labels(const Grid& g, const uint16_t* L0, const float* u, uint16_t* dst,
+                   cudaStream_t s);
+void launch_downsample(const Grid& fine, const Grid& coarse, int factor, const float* src,
+                       float* dst, cudaStream_t s);
+void launch_upsample(const Grid& coarse, const Grid& fine, float ratio, const float* src,
+                     float* dst, int nfields, cudaStream_t s);
+void launch_check_finite(const float* a, int64_t n, int* flag, cudaStream_t s);
+void launch_fill(float* a, int64_t n, float value, cudaStream_t s);
+void launch_dice_hist(const uint16_t* A, const uint16_t* B, int64_t n,
+                      unsigned long long* hist /* 3 x 65536 */, cudaStream_t s);
+
+// ---- smoothing operator K (kernels_dft.cu) ----
+struct KPlan {
+  int nx, ny, nz;
+  float alpha, gamma;
+  // per-axis orthonormal real DFT matrices R (row k = frequency basis vector), row-major
+  float* Rx; float* Ry; float* Rz;
+  // per-axis discrete-Laplacian eigenvalue of each row, lambda_d(row) / h_d^2 folded in
+  float* lx; float* ly; float* lz;
+  // bf16 hi/lo splits of R for the tensor-core path (row-major, same shape)
+  uint16_t *Rx_hi, *Rx_lo, *Ry_hi, *Ry_lo, *Rz_hi, *Rz_lo;
+};
+// Build device tables for one grid (allocates; free with kplan_destroy).
+cudaError_t kplan_create(KPlan* kp, int nx, int ny, int nz, float hx, float hy, float hz,
+                         float alpha, float gamma);
+void kplan_destroy(KPlan* kp);
+// out = K in for `ncomp` scalar fields stored back to back (each nx*ny*nz); work needs
+// ncomp*N floats.  in and out may alias.  mode: LDDMM_K_*.
+cudaError_t apply_K(const KPlan& kp, int mode, const float* in, float* out, float* work,
+                    int ncomp, cudaStream_t s, const Hook& hook = Hook());
+
+}  // namespace lddmm

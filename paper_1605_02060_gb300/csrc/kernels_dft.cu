@@ -1,0 +1,247 @@
+// The smoothing operator K = (gamma - alpha Lap_h)^-2 of §2.4 (K = (L^T L)^-1 for
+// L = -alpha Lap + gamma), applied on the periodic grid as separable per-axis real DFTs.
+//
+// For an axis of length n, R is the orthonormal real Fourier basis (rows: constant, then
+// cos/sin pairs of frequency k = 1.., then the Nyquist cosine when n is even).  The symbol of
+// K depends on each frequency only through lambda(k) = sum_d (2 - 2 cos(2 pi k_d / n_d)) / h_d^2,
+// which is the same for the cos and the sin row of a pair, so with R3 = Rz (x) Ry (x) Rx
+//     K = R3^T diag((gamma + alpha lambda)^-2) R3.
+// Each axis transform is a dense matrix product over all lines of that axis: a batched GEMM
+// whose small operand is R (n x n) and whose large operand is the field.  The symbol scaling is
+// fused into the epilogue of the forward z product.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "../../include/lddmm.h"
+#include "kernels.h"
+
+namespace lddmm {
+
+// ---------------------------------------------------------------------------------------------
+// Table construction (host, double precision, angles reduced modulo n).
+static void real_dft_matrix(int n, double h, std::vector<float>& R, std::vector<float>& lam) {
+  R.assign((size_t)n * n, 0.f);
+  lam.assign(n, 0.f);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int r = 0; r < n; ++r) {
+    const int k = (r + 1) / 2;
+    const bool is_sin = (r > 0) && (r % 2 == 0);
+    const bool nyq = (n % 2 == 0) && (r == n - 1);
+    const double scale = (r == 0 || nyq) ? std::sqrt(1.0 / n) : std::sqrt(2.0 / n);
+    for (int m = 0; m < n; ++m) {
+      const double ang = two_pi * (double)(((long long)k * m) % n) / (double)n;
+      R[(size_t)r * n + m] = (float)(scale * (is_sin ? std::sin(ang) : std::cos(ang)));
+    }
+    lam[r] = (float)((2.0 - 2.0 * std::cos(two_pi * (double)k / (double)n)) / (h * h));
+  }
+}
+
+static uint16_t bf16_rn(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;
+  return (uint16_t)(u >> 16);
+}
+static float bf16_to_f(uint16_t b) {
+  uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+template <typename T>
+static cudaError_t upload(T** dst, const std::vector<T>& src) {
+  cudaError_t e = cudaMalloc((void**)dst, src.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+cudaError_t kplan_create(KPlan* kp, int nx, int ny, int nz, float hx, float hy, float hz,
+                         float alpha, float gamma) {
+  *kp = KPlan{};
+  kp->nx = nx; kp->ny = ny; kp->nz = nz;
+  kp->alpha = alpha; kp->gamma = gamma;
+  const int n[3] = {nx, ny, nz};
+  const double h[3] = {hx, hy, hz};
+  float** Rs[3] = {&kp->Rx, &kp->Ry, &kp->Rz};
+  float** ls[3] = {&kp->lx, &kp->ly, &kp->lz};
+  uint16_t** his[3] = {&kp->Rx_hi, &kp->Ry_hi, &kp->Rz_hi};
+  uint16_t** los[3] = {&kp->Rx_lo, &kp->Ry_lo, &kp->Rz_lo};
+  for (int d = 0; d < 3; ++d) {
+    std::vector<float> R, lam;
+    real_dft_matrix(n[d], h[d], R, lam);
+    std::vector<uint16_t> hi(R.size()), lo(R.size());
+    for (size_t i = 0; i < R.size(); ++i) {
+      hi[i] = bf16_rn(R[i]);
+      lo[i] = bf16_rn(R[i] - bf16_to_f(hi[i]));
+    }
+    cudaError_t e;
+    if ((e = upload(Rs[d], R)) != cudaSuccess) return e;
+    if ((e = upload(ls[d], lam)) != cudaSuccess) return e;
+    if ((e = upload(his[d], hi)) != cudaSuccess) return e;
+    if ((e = upload(los[d], lo)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+void kplan_destroy(KPlan* kp) {
+  void* ps[] = {kp->Rx, kp->Ry, kp->Rz, kp->lx, kp->ly, kp->lz,
+                kp->Rx_hi, kp->Rx_lo, kp->Ry_hi, kp->Ry_lo, kp->Rz_hi, kp->Rz_lo};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  *kp = KPlan{};
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP32 batched GEMM on the CUDA cores: C_b(m,n) = sum_k A_b(m,k) B_b(k,n), arbitrary strides.
+// 64x64 output tile per block, k-slices of 16 staged in shared memory, 4x4 per thread.
+struct GemmArgs {
+  int M, N, K, batch;
+  const float* A; long long sAb, sAm, sAk;
+  const float* B; long long sBb, sBk, sBn;
+  float* C; long long sCb, sCm, sCn;
+  // optional symbol epilogue (forward z): C(m,n) *= (gamma + alpha (lz[m] + ly[n/nx] + lx[n%nx]))^-2
+  const float* lx; const float* ly; const float* lz; int nx; float alpha, gamma;
+};
+
+constexpr int TBM = 64, TBN = 64, TBK = 16;
+
+__global__ void __launch_bounds__(256) k_sgemm(GemmArgs a) {
+  __shared__ float As[TBK][TBM + 4];
+  __shared__ float Bs[TBK][TBN + 4];
+  const int b = blockIdx.z;
+  const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+  const float* A = a.A + b * a.sAb;
+  const float* B = a.B + b * a.sBb;
+  float* C = a.C + b * a.sCb;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  float acc[4][4] = {};
+  const bool a_kfast = (a.sAk == 1);
+  const bool b_nfast = (a.sBn == 1);
+  for (int k0 = 0; k0 < a.K; k0 += TBK) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + i * 256;
+      int mm, kk;
+      if (a_kfast) { mm = e / TBK; kk = e % TBK; } else { kk = e / TBM; mm = e % TBM; }
+      const int gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < a.M && gk < a.K) ? A[gm * a.sAm + gk * a.sAk] : 0.f;
+      int nn, kb;
+      if (b_nfast) { kb = e / TBN; nn = e % TBN; } else { nn = e / TBK; kb = e % TBK; }
+      const int gn = n0 + nn, gk2 = k0 + kb;
+      Bs[kb][nn] = (gn < a.N && gk2 < a.K) ? B[gk2 * a.sBk + gn * a.sBn] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TBK; ++kk) {
+      float av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= a.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn >= a.N) continue;
+      float v = acc[i][j];
+      if (a.lz) {
+        const float lam = a.lz[gm] + a.ly[gn / a.nx] + a.lx[gn % a.nx];
+        const float den = a.gamma + a.alpha * lam;
+        v = v / (den * den);
+      }
+      C[gm * a.sCm + gn * a.sCn] = v;
+    }
+  }
+}
+
+static void sgemm(const GemmArgs& a, cudaStream_t s) {
+  dim3 grid((a.N + TBN - 1) / TBN, (a.M + TBM - 1) / TBM, a.batch);
+  k_sgemm<<<grid, 256, 0, s>>>(a);
+}
+
+static GemmArgs gemm_x(const KPlan& kp, int ncomp, const float* in, float* out, bool fwd) {
+  // rows of length nx: out[row][n] = sum_k in[row][k] B(k,n); B(k,n) = R[n][k] (fwd) or R[k][n]
+  const int L = kp.nx;
+  GemmArgs a{};
+  a.M = ncomp * kp.ny * kp.nz; a.N = L; a.K = L; a.batch = 1;
+  a.A = in; a.sAm = L; a.sAk = 1;
+  a.B = kp.Rx;
+  if (fwd) { a.sBk = 1; a.sBn = L; } else { a.sBk = L; a.sBn = 1; }
+  a.C = out; a.sCm = L; a.sCn = 1;
+  return a;
+}
+
+static GemmArgs gemm_left(const float* R, int L, long long stride_k, long long ncols,
+                          int batch, long long sbatch, const float* in, float* out, bool fwd) {
+  // out_b[r][n] = sum_m A(r,m) in_b[m][n]; A = R (fwd) or R^T (inverse)
+  GemmArgs a{};
+  a.M = L; a.K = L; a.N = (int)ncols; a.batch = batch;
+  a.A = R;
+  if (fwd) { a.sAm = L; a.sAk = 1; } else { a.sAm = 1; a.sAk = L; }
+  a.sAb = 0;
+  a.B = in; a.sBb = sbatch; a.sBk = stride_k; a.sBn = 1;
+  a.C = out; a.sCb = sbatch; a.sCm = stride_k; a.sCn = 1;
+  return a;
+}
+
+static cudaError_t apply_K_fp32(const KPlan& kp, const float* in, float* out, float* work,
+                                int ncomp, cudaStream_t s, const Hook& hook) {
+  const long long nxy = (long long)kp.nx * kp.ny;
+  const long long N = nxy * kp.nz;
+  // forward x: in -> work
+  hook(KID_KX_FWD, 0);
+  sgemm(gemm_x(kp, ncomp, in, work, true), s);
+  hook(KID_KX_FWD, 1);
+  // forward y: work -> out   (batches: ncomp * nz planes of ny x nx)
+  hook(KID_KY_FWD, 0);
+  sgemm(gemm_left(kp.Ry, kp.ny, kp.nx, kp.nx, ncomp * kp.nz, nxy, work, out, true), s);
+  hook(KID_KY_FWD, 1);
+  // forward z with the symbol: out -> work (batches: ncomp volumes, nz x (ny nx))
+  {
+    GemmArgs a = gemm_left(kp.Rz, kp.nz, nxy, nxy, ncomp, N, out, work, true);
+    a.lx = kp.lx; a.ly = kp.ly; a.lz = kp.lz; a.nx = kp.nx;
+    a.alpha = kp.alpha; a.gamma = kp.gamma;
+    hook(KID_KZ_SYM, 0);
+    sgemm(a, s);
+    hook(KID_KZ_SYM, 1);
+  }
+  // inverse z: work -> out
+  hook(KID_KZ_INV, 0);
+  sgemm(gemm_left(kp.Rz, kp.nz, nxy, nxy, ncomp, N, work, out, false), s);
+  hook(KID_KZ_INV, 1);
+  // inverse y: out -> work
+  hook(KID_KY_INV, 0);
+  sgemm(gemm_left(kp.Ry, kp.ny, kp.nx, kp.nx, ncomp * kp.nz, nxy, out, work, false), s);
+  hook(KID_KY_INV, 1);
+  // inverse x: work -> out
+  hook(KID_KX_INV, 0);
+  sgemm(gemm_x(kp, ncomp, work, out, false), s);
+  hook(KID_KX_INV, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t apply_K(const KPlan& kp, int mode, const float* in, float* out, float* work,
+                    int ncomp, cudaStream_t s, const Hook& hook) {
+  switch (mode) {
+    case LDDMM_K_FP32:
+      return apply_K_fp32(kp, in, out, work, ncomp, s, hook);
+    default:
+      return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace lddmm

@@ -1,0 +1,733 @@
+// C ABI of liblddmm: context, buffers, the multiscale schedule and one gradient-descent
+// iteration of masked LDDMM (§2.4 of Kutten et al., SPIE 2016; Beg et al. 2005 update).
+// Host code only; every step of the computation runs in the kernels of kernels_*.cu.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/lddmm.h"
+#include "kernels.h"
+
+using namespace lddmm;
+
+namespace {
+
+thread_local std::string g_global_error;
+
+struct Level {
+  Grid g;
+  int factor;
+  float hx, hy, hz;
+  float *I0 = nullptr, *I1 = nullptr, *M = nullptr;
+  KPlan kp{};
+};
+
+}  // namespace
+
+struct lddmm_ctx {
+  lddmm_params p{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<Level> levels;
+  int cur = 0;
+  int64_t Nmax = 0;
+  // working buffers, sized for the finest level
+  float* v = nullptr;       // [T][3][N]
+  float* v_tmp = nullptr;   // [T][3][N] resampling / backtracking copy
+  float* v_prev = nullptr;  // [T][3][N] v before the last accepted update (backtracking)
+  bool have_prev = false;
+  float* uB[2] = {nullptr, nullptr};
+  float* uF[2] = {nullptr, nullptr};
+  float* J1 = nullptr;      // [T][N]
+  float* W = nullptr;       // [T][N]
+  float* b = nullptr;       // [3][N]
+  float* work = nullptr;    // [3][N]
+  float* J0T = nullptr;     // [N]
+  float* stage = nullptr;   // [3][N] staging for host inputs / outputs
+  Acc* acc = nullptr;
+  Acc* acc_host = nullptr;  // pinned
+  int* flag = nullptr;      // device int
+  unsigned long long* hist = nullptr;  // 3 x 65536
+  // map state
+  const float* u10 = nullptr;
+  const float* u01 = nullptr;
+  bool maps_valid = false;
+  bool j0_valid = false;
+  int iter = 0;
+  double last_E = -1.0;
+  float eps = 0.f;
+  std::string err;
+  // timing of every kernel launch (lddmm_profile_start / lddmm_profile_stop)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;   // 2 per launch
+  std::vector<int> prof_kid;
+  size_t prof_used = 0;
+  bool prof_overflow = false;
+  int prof_open = -1;
+};
+
+namespace {
+
+int fail(lddmm_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_global_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? LDDMM_ERR_OOM : LDDMM_ERR_CUDA,      \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int wait_stream(lddmm_ctx* ctx) {
+  const double limit = ctx->p.timeout_s > 0 ? ctx->p.timeout_s : 600.0;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaStreamQuery(ctx->stream);
+    if (e == cudaSuccess) return LDDMM_OK;
+    if (e != cudaErrorNotReady)
+      return fail(ctx, LDDMM_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+    const double el =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > limit) return fail(ctx, LDDMM_ERR_TIMEOUT, "timed out waiting for the GPU stream");
+    std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 5 : 200));
+  }
+}
+
+void prof_mark(void* user, int kid, int phase) {
+  lddmm_ctx* ctx = static_cast<lddmm_ctx*>(user);
+  if (!ctx->prof_on) return;
+  if (phase == 0) {
+    if (ctx->prof_used >= ctx->prof_kid.size()) { ctx->prof_overflow = true; ctx->prof_open = -1; return; }
+    cudaEventRecord(ctx->prof_ev[2 * ctx->prof_used], ctx->stream);
+    ctx->prof_open = kid;
+  } else if (ctx->prof_open == kid) {
+    cudaEventRecord(ctx->prof_ev[2 * ctx->prof_used + 1], ctx->stream);
+    ctx->prof_kid[ctx->prof_used++] = kid;
+    ctx->prof_open = -1;
+  }
+}
+
+Hook hook_of(lddmm_ctx* ctx) {
+  Hook h;
+  if (ctx->prof_on) { h.mark = prof_mark; h.user = ctx; }
+  return h;
+}
+
+const char* kernel_name(int kid) {
+  static const char* names[KID_COUNT] = {"flow_back_disp", "flow_back_terms", "fwd_residual",
+                                         "fwd_flow_ereg", "K_x_fwd", "K_y_fwd", "K_z_symbol",
+                                         "K_z_inv", "K_y_inv", "K_x_inv_update", "update"};
+  return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
+}
+
+int validate(const lddmm_params* p, std::string& why) {
+  if (!p) { why = "params is NULL"; return LDDMM_ERR_INVALID_ARG; }
+  if (p->nx < 2 || p->ny < 2 || p->nz < 2) { why = "grid sizes must be >= 2"; return LDDMM_ERR_INVALID_ARG; }
+  const int64_t N = (int64_t)p->nx * p->ny * p->nz;
+  if (N * 3 >= (int64_t)1 << 31) { why = "grid too large (3*nx*ny*nz must be < 2^31)"; return LDDMM_ERR_INVALID_ARG; }
+  if (!(p->hx > 0 && p->hy > 0 && p->hz > 0)) { why = "spacing must be > 0"; return LDDMM_ERR_INVALID_ARG; }
+  if (p->T < 1 || p->T > 1000) { why = "T must be in [1, 1000]"; return LDDMM_ERR_INVALID_ARG; }
+  if (!(p->alpha >= 0 && std::isfinite(p->alpha))) { why = "alpha must be >= 0"; return LDDMM_ERR_INVALID_ARG; }
+  if (!(p->gamma > 0 && std::isfinite(p->gamma))) { why = "gamma must be > 0"; return LDDMM_ERR_INVALID_ARG; }
+  if (!(p->sigma > 0 && std::isfinite(p->sigma))) { why = "sigma must be > 0"; return LDDMM_ERR_INVALID_ARG; }
+  if (!(p->epsilon > 0 && std::isfinite(p->epsilon))) { why = "epsilon must be > 0"; return LDDMM_ERR_INVALID_ARG; }
+  if (p->iterations < 0) { why = "iterations must be >= 0"; return LDDMM_ERR_INVALID_ARG; }
+  if (p->num_levels < 1 || p->num_levels > 4) { why = "num_levels must be in [1, 4]"; return LDDMM_ERR_INVALID_ARG; }
+  for (int l = 0; l < p->num_levels; ++l) {
+    const int f = p->level_factor[l];
+    if (f < 1 || f > 64) { why = "level factors must be in [1, 64]"; return LDDMM_ERR_INVALID_ARG; }
+    if (l > 0 && f >= p->level_factor[l - 1]) { why = "level factors must decrease"; return LDDMM_ERR_INVALID_ARG; }
+    if ((p->nx + f - 1) / f < 2 || (p->ny + f - 1) / f < 2 || (p->nz + f - 1) / f < 2) {
+      why = "a level grid has an axis shorter than 2"; return LDDMM_ERR_INVALID_ARG;
+    }
+  }
+  if (p->level_factor[p->num_levels - 1] != 1) { why = "the last level factor must be 1"; return LDDMM_ERR_INVALID_ARG; }
+  if (p->k_mode < LDDMM_K_FP32 || p->k_mode > LDDMM_K_BF16) { why = "unknown k_mode"; return LDDMM_ERR_INVALID_ARG; }
+  if (p->flags & ~1) { why = "unknown flag bits"; return LDDMM_ERR_INVALID_ARG; }
+  return LDDMM_OK;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, int64_t n) {
+  return cudaMalloc((void**)p, (size_t)n * sizeof(T));
+}
+
+const float* field_src(lddmm_ctx* ctx, const float* user, int64_t n, float* stage, int* rc) {
+  // Device pointers are used in place; host pointers are copied to the staging buffer.
+  *rc = LDDMM_OK;
+  if (is_device_ptr(user)) return user;
+  cudaError_t e = cudaMemcpyAsync(stage, user, n * sizeof(float), cudaMemcpyDefault, ctx->stream);
+  if (e != cudaSuccess) {
+    *rc = fail(ctx, LDDMM_ERR_CUDA, cudaGetErrorString(e));
+    return nullptr;
+  }
+  return stage;
+}
+
+int check_finite(lddmm_ctx* ctx, const float* d, int64_t n, const char* what) {
+  CK(cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->stream));
+  launch_check_finite(d, n, ctx->flag, ctx->stream);
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  if (h) return fail(ctx, LDDMM_ERR_NONFINITE, std::string(what) + " holds NaN or Inf");
+  return LDDMM_OK;
+}
+
+int load_images(lddmm_ctx* ctx, const float* I0, const float* I1, const float* M) {
+  Level& F = ctx->levels.back();
+  const int64_t N = F.g.N;
+  CK(cudaMemcpyAsync(F.I0, I0, N * sizeof(float), cudaMemcpyDefault, ctx->stream));
+  CK(cudaMemcpyAsync(F.I1, I1, N * sizeof(float), cudaMemcpyDefault, ctx->stream));
+  if (M) CK(cudaMemcpyAsync(F.M, M, N * sizeof(float), cudaMemcpyDefault, ctx->stream));
+  else launch_fill(F.M, N, 1.0f, ctx->stream);
+  CK(cudaGetLastError());
+  int rc;
+  if ((rc = check_finite(ctx, F.I0, N, "I0"))) return rc;
+  if ((rc = check_finite(ctx, F.I1, N, "I1"))) return rc;
+  if ((rc = check_finite(ctx, F.M, N, "M"))) return rc;
+  for (size_t l = 0; l + 1 < ctx->levels.size(); ++l) {
+    Level& L = ctx->levels[l];
+    launch_downsample(F.g, L.g, L.factor, F.I0, L.I0, ctx->stream);
+    launch_downsample(F.g, L.g, L.factor, F.I1, L.I1, ctx->stream);
+    launch_downsample(F.g, L.g, L.factor, F.M, L.M, ctx->stream);
+  }
+  CK(cudaGetLastError());
+  ctx->maps_valid = false;
+  ctx->j0_valid = false;
+  return LDDMM_OK;
+}
+
+void release(lddmm_ctx* ctx) {
+  for (Level& L : ctx->levels) {
+    cudaFree(L.I0); cudaFree(L.I1); cudaFree(L.M);
+    kplan_destroy(&L.kp);
+  }
+  void* ps[] = {ctx->v, ctx->v_tmp, ctx->v_prev, ctx->uB[0], ctx->uB[1], ctx->uF[0], ctx->uF[1], ctx->J1,
+                ctx->W, ctx->b, ctx->work, ctx->J0T, ctx->stage, ctx->acc, ctx->flag, ctx->hist};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  if (ctx->acc_host) cudaFreeHost(ctx->acc_host);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+}
+
+inline float dtv(const lddmm_ctx* ctx, float h) { return 1.0f / (float)ctx->p.T / h; }
+
+int reset_acc(lddmm_ctx* ctx) {
+  Acc a{};
+  a.min_det_ord = 0x7f7fffff;  // +FLT_MAX in the ordered encoding
+  CK(cudaMemcpyAsync(ctx->acc, &a, sizeof(Acc), cudaMemcpyHostToDevice, ctx->stream));
+  return LDDMM_OK;
+}
+
+double ordered_to_float(int i) {
+  const int b = i >= 0 ? i : i ^ 0x7fffffff;
+  float f;
+  std::memcpy(&f, &b, 4);
+  return (double)f;
+}
+
+int read_energy(lddmm_ctx* ctx, lddmm_energy* out, bool with_det) {
+  CK(cudaMemcpyAsync(ctx->acc_host, ctx->acc, sizeof(Acc), cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  const Level& L = ctx->levels[ctx->cur];
+  const double h3 = (double)L.hx * L.hy * L.hz;
+  const double s = ctx->p.sigma;
+  out->reg = ctx->acc_host->e_reg * h3 / (double)ctx->p.T;
+  out->data = ctx->acc_host->e_data * h3 / (s * s);
+  out->total = out->reg + out->data;
+  out->min_det = with_det ? ordered_to_float(ctx->acc_host->min_det_ord) : 1.0;
+  out->fold = with_det && out->min_det <= 0.0;
+  out->iter = ctx->iter - 1;
+  out->level = ctx->cur;
+  out->pad = 0;
+  if (!std::isfinite(out->total)) return fail(ctx, LDDMM_ERR_NONFINITE, "energy is not finite");
+  return LDDMM_OK;
+}
+
+// One iteration: backward sweep, forward sweep with K and the update per time step.
+int run_step(lddmm_ctx* ctx) {
+  const Level& L = ctx->levels[ctx->cur];
+  const Grid& g = L.g;
+  const int T = ctx->p.T;
+  const int64_t N = g.N;
+  cudaStream_t s = ctx->stream;
+  const float dtx = dtv(ctx, L.hx), dty = dtv(ctx, L.hy), dtz = dtv(ctx, L.hz);
+  const Hook hk = hook_of(ctx);
+  int rc = reset_acc(ctx);
+  if (rc) return rc;
+  // backward sweep j = T-1 .. 0
+  const float* un = nullptr;
+  int pb = 0;
+  for (int j = T - 1; j >= 0; --j) {
+    float* uc = ctx->uB[pb];
+    launch_flow_back(g, ctx->v + (int64_t)j * 3 * N, un, uc, L.I1, L.M, ctx->J1 + j * N,
+                     ctx->W + j * N, dtx, dty, dtz, ctx->acc, s, hk);
+    un = uc;
+    pb ^= 1;
+  }
+  ctx->u01 = un;
+  // forward sweep j = 0 .. T-1 with smoothing and update
+  const float c = 2.0f / (ctx->p.sigma * ctx->p.sigma);
+  const float* uc = nullptr;
+  int pf = 0;
+  for (int j = 0; j < T; ++j) {
+    float* vj = ctx->v + (int64_t)j * 3 * N;
+    hk(KID_FWD_TERMS, 0);
+    launch_fwd_terms(g, uc, L.I0, ctx->J1 + j * N, ctx->W + j * N, ctx->b, c, 1.0f / L.hx,
+                     1.0f / L.hy, 1.0f / L.hz, s);
+    hk(KID_FWD_TERMS, 1);
+    float* unx = ctx->uF[pf];
+    hk(KID_FWD_FLOW, 0);
+    launch_fwd_flow(g, vj, uc, unx, dtx, dty, dtz, ctx->p.alpha, ctx->p.gamma,
+                    1.0f / (L.hx * L.hx), 1.0f / (L.hy * L.hy), 1.0f / (L.hz * L.hz), j == T - 1,
+                    L.I0, L.I1, L.M, ctx->J0T, ctx->acc, s);
+    hk(KID_FWD_FLOW, 1);
+    CK(apply_K(L.kp, ctx->p.k_mode, ctx->b, ctx->b, ctx->work, 3, s, hk));
+    hk(KID_UPDATE, 0);
+    launch_update(g, vj, ctx->b, ctx->eps, s);
+    hk(KID_UPDATE, 1);
+    uc = unx;
+    pf ^= 1;
+  }
+  ctx->u10 = uc;
+  CK(cudaGetLastError());
+  // The maps and J0_T describe the velocity before the update.
+  ctx->maps_valid = false;
+  ctx->j0_valid = false;
+  return LDDMM_OK;
+}
+
+// Recompute phi_{1,0}, phi_{0,1} (and optionally J0_T, the energy) for the current v.
+int refresh_maps(lddmm_ctx* ctx, bool energy) {
+  const Level& L = ctx->levels[ctx->cur];
+  const Grid& g = L.g;
+  const int T = ctx->p.T;
+  const int64_t N = g.N;
+  cudaStream_t s = ctx->stream;
+  const float dtx = dtv(ctx, L.hx), dty = dtv(ctx, L.hy), dtz = dtv(ctx, L.hz);
+  int rc = reset_acc(ctx);
+  if (rc) return rc;
+  const float* un = nullptr;
+  int pb = 0;
+  for (int j = T - 1; j >= 0; --j) {
+    float* uc = ctx->uB[pb];
+    launch_flow_only_back(g, ctx->v + (int64_t)j * 3 * N, un, uc, dtx, dty, dtz, s);
+    un = uc;
+    pb ^= 1;
+  }
+  ctx->u01 = un;
+  const float* uc = nullptr;
+  int pf = 0;
+  for (int j = 0; j < T; ++j) {
+    float* unx = ctx->uF[pf];
+    launch_fwd_flow(g, ctx->v + (int64_t)j * 3 * N, uc, unx, dtx, dty, dtz, ctx->p.alpha,
+                    ctx->p.gamma, 1.0f / (L.hx * L.hx), 1.0f / (L.hy * L.hy),
+                    1.0f / (L.hz * L.hz), j == T - 1, L.I0, L.I1, L.M, ctx->J0T, ctx->acc, s);
+    uc = unx;
+    pf ^= 1;
+  }
+  ctx->u10 = uc;
+  CK(cudaGetLastError());
+  ctx->maps_valid = true;
+  ctx->j0_valid = true;
+  (void)energy;
+  return LDDMM_OK;
+}
+
+int copy_out(lddmm_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream));
+  if (!is_device_ptr(dst)) return wait_stream(ctx);
+  return LDDMM_OK;
+}
+
+int change_level(lddmm_ctx* ctx, int level) {
+  if (level == ctx->cur) return LDDMM_OK;
+  const Level& A = ctx->levels[ctx->cur];
+  const Level& B = ctx->levels[level];
+  const int T = ctx->p.T;
+  launch_upsample(A.g, B.g, (float)B.factor / (float)A.factor, ctx->v, ctx->v_tmp, 3 * T,
+                  ctx->stream);
+  CK(cudaGetLastError());
+  std::swap(ctx->v, ctx->v_tmp);
+  ctx->cur = level;
+  ctx->maps_valid = false;
+  ctx->j0_valid = false;
+  ctx->last_E = -1.0;
+  ctx->have_prev = false;
+  return LDDMM_OK;
+}
+
+int do_step(lddmm_ctx* ctx, lddmm_energy* out) {
+  // flags bit 0: backtracking.  If E(v_k) > E(v_{k-1}), the previous update overshot: go back
+  // to v_{k-1} (kept in v_prev), halve the step and redo that iteration.
+  const bool backtrack = (ctx->p.flags & 1) != 0;
+  const Level& L = ctx->levels[ctx->cur];
+  const size_t vbytes = (size_t)ctx->p.T * 3 * L.g.N * sizeof(float);
+  for (int attempt = 0; attempt < 30; ++attempt) {
+    if (backtrack) CK(cudaMemcpyAsync(ctx->v_tmp, ctx->v, vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    int rc = run_step(ctx);
+    if (rc) return rc;
+    ++ctx->iter;  // counts enqueued iterations, also when a later wait times out
+    if (!out && !backtrack) return LDDMM_OK;
+    lddmm_energy e{};
+    rc = read_energy(ctx, &e, true);
+    if (rc) return rc;
+    if (backtrack && ctx->have_prev && e.total > ctx->last_E) {
+      CK(cudaMemcpyAsync(ctx->v, ctx->v_prev, vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      ctx->eps *= 0.5f;
+      ctx->have_prev = false;
+      --ctx->iter;
+      continue;
+    }
+    if (backtrack) { std::swap(ctx->v_prev, ctx->v_tmp); ctx->have_prev = true; }
+    ctx->last_E = e.total;
+    if (out) *out = e;
+    return LDDMM_OK;
+  }
+  return fail(ctx, LDDMM_ERR_STATE, "backtracking did not find a decreasing step");
+}
+
+}  // namespace
+
+extern "C" {
+
+int lddmm_default_params(lddmm_params* p, int nx, int ny, int nz) {
+  if (!p) return fail(nullptr, LDDMM_ERR_INVALID_ARG, "params is NULL");
+  std::memset(p, 0, sizeof(*p));
+  p->nx = nx; p->ny = ny; p->nz = nz;
+  p->hx = p->hy = p->hz = 1.0f;
+  p->T = 10;
+  p->alpha = 0.02f; p->gamma = 1.0f; p->sigma = 0.1f;
+  p->epsilon = 1e-3f;
+  p->iterations = 20;
+  p->num_levels = 1;
+  p->level_factor[0] = 1;
+  p->k_mode = LDDMM_K_FP32;
+  p->flags = 0;
+  p->timeout_s = 600.0f;
+  return LDDMM_OK;
+}
+
+int lddmm_create(const lddmm_params* p, const float* I0, const float* I1, const float* M,
+                 void* stream, lddmm_ctx** out) {
+  if (!out) return fail(nullptr, LDDMM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  int rc = validate(p, why);
+  if (rc) return fail(nullptr, rc, why);
+  if (!I0 || !I1) return fail(nullptr, LDDMM_ERR_INVALID_ARG, "I0 and I1 are required");
+  lddmm_ctx* ctx = new (std::nothrow) lddmm_ctx();
+  if (!ctx) return fail(nullptr, LDDMM_ERR_OOM, "host allocation failed");
+  ctx->p = *p;
+  ctx->eps = p->epsilon;
+  auto bail = [&](int code) {
+    std::string msg = ctx->err;
+    release(ctx);
+    delete ctx;
+    return fail(nullptr, code, msg);
+  };
+  if (stream) {
+    ctx->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      ctx->err = "could not create a CUDA stream (no usable GPU?)";
+      return bail(LDDMM_ERR_CUDA);
+    }
+    ctx->own_stream = true;
+  }
+  const int nl = p->num_levels;
+  ctx->levels.resize(nl);
+  for (int l = 0; l < nl; ++l) {
+    Level& L = ctx->levels[l];
+    L.factor = p->level_factor[l];
+    L.g.nx = (p->nx + L.factor - 1) / L.factor;
+    L.g.ny = (p->ny + L.factor - 1) / L.factor;
+    L.g.nz = (p->nz + L.factor - 1) / L.factor;
+    L.g.N = L.g.nx * L.g.ny * L.g.nz;
+    L.hx = p->hx * L.factor; L.hy = p->hy * L.factor; L.hz = p->hz * L.factor;
+  }
+  const int64_t N = ctx->levels.back().g.N;
+  ctx->Nmax = N;
+  const int64_t T = p->T;
+  auto A = [&](cudaError_t e) {
+    if (e != cudaSuccess) {
+      ctx->err = std::string("device allocation: ") + cudaGetErrorString(e);
+      return false;
+    }
+    return true;
+  };
+  bool ok = true;
+  for (int l = 0; l < nl && ok; ++l) {
+    Level& L = ctx->levels[l];
+    ok = A(dalloc(&L.I0, L.g.N)) && A(dalloc(&L.I1, L.g.N)) && A(dalloc(&L.M, L.g.N)) &&
+         A(kplan_create(&L.kp, L.g.nx, L.g.ny, L.g.nz, L.hx, L.hy, L.hz, p->alpha, p->gamma));
+  }
+  ok = ok && A(dalloc(&ctx->v, T * 3 * N)) && A(dalloc(&ctx->v_tmp, T * 3 * N)) &&
+       A(dalloc(&ctx->uB[0], 3 * N)) && A(dalloc(&ctx->uB[1], 3 * N)) &&
+       A(dalloc(&ctx->uF[0], 3 * N)) && A(dalloc(&ctx->uF[1], 3 * N)) &&
+       A(dalloc(&ctx->J1, T * N)) && A(dalloc(&ctx->W, T * N)) && A(dalloc(&ctx->b, 3 * N)) &&
+       A(dalloc(&ctx->work, 3 * N)) && A(dalloc(&ctx->J0T, N)) && A(dalloc(&ctx->stage, 3 * N)) &&
+       A(dalloc(&ctx->acc, 1)) && A(dalloc(&ctx->flag, 1)) && A(dalloc(&ctx->hist, 3 * 65536)) &&
+       A(cudaMallocHost((void**)&ctx->acc_host, sizeof(Acc)));
+  if (ok && (p->flags & 1)) ok = A(dalloc(&ctx->v_prev, T * 3 * N));
+  if (!ok) return bail(LDDMM_ERR_OOM);
+  if (cudaMemsetAsync(ctx->v, 0, (size_t)T * 3 * N * sizeof(float), ctx->stream) != cudaSuccess) {
+    ctx->err = "memset failed";
+    return bail(LDDMM_ERR_CUDA);
+  }
+  rc = load_images(ctx, I0, I1, M);
+  if (rc) return bail(rc);
+  ctx->cur = 0;
+  *out = ctx;
+  return LDDMM_OK;
+}
+
+int lddmm_set_images(lddmm_ctx* ctx, const float* I0, const float* I1, const float* M) {
+  if (!ctx || !I0 || !I1) return fail(ctx, LDDMM_ERR_INVALID_ARG, "NULL argument");
+  return load_images(ctx, I0, I1, M);
+}
+
+int lddmm_step(lddmm_ctx* ctx, lddmm_energy* out) {
+  if (!ctx) return fail(nullptr, LDDMM_ERR_INVALID_ARG, "ctx is NULL");
+  return do_step(ctx, out);
+}
+
+int lddmm_register(lddmm_ctx* ctx, lddmm_energy* trace, int trace_len) {
+  if (!ctx) return fail(nullptr, LDDMM_ERR_INVALID_ARG, "ctx is NULL");
+  if (trace_len < 0 || (trace_len > 0 && !trace)) return fail(ctx, LDDMM_ERR_INVALID_ARG, "bad trace");
+  int k = 0;
+  for (int l = ctx->cur; l < (int)ctx->levels.size(); ++l) {
+    int rc = change_level(ctx, l);
+    if (rc) return rc;
+    for (int it = 0; it < ctx->p.iterations; ++it) {
+      lddmm_energy e{};
+      rc = do_step(ctx, k < trace_len ? &e : nullptr);
+      if (rc) return rc;
+      if (k < trace_len) trace[k] = e;
+      ++k;
+    }
+  }
+  return wait_stream(ctx);
+}
+
+int lddmm_set_level(lddmm_ctx* ctx, int level) {
+  if (!ctx) return fail(nullptr, LDDMM_ERR_INVALID_ARG, "ctx is NULL");
+  if (level < 0 || level >= (int)ctx->levels.size()) return fail(ctx, LDDMM_ERR_INVALID_ARG, "bad level");
+  return change_level(ctx, level);
+}
+
+int lddmm_grid(lddmm_ctx* ctx, int* nx, int* ny, int* nz, int* level) {
+  if (!ctx) return fail(nullptr, LDDMM_ERR_INVALID_ARG, "ctx is NULL");
+  const Grid& g = ctx->levels[ctx->cur].g;
+  if (nx) *nx = g.nx;
+  if (ny) *ny = g.ny;
+  if (nz) *nz = g.nz;
+  if (level) *level = ctx->cur;
+  return LDDMM_OK;
+}
+
+int lddmm_warp(lddmm_ctx* ctx, const float* src, float* dst, int direction) {
+  if (!ctx || !src || !dst) return fail(ctx, LDDMM_ERR_INVALID_ARG, "NULL argument");
+  if (direction != 0 && direction != 1) return fail(ctx, LDDMM_ERR_INVALID_ARG, "direction must be 0 or 1");
+  int rc;
+  if (!ctx->maps_valid && (rc = refresh_maps(ctx, false))) return rc;
+  const Grid& g = ctx->levels[ctx->cur].g;
+  const float* s = field_src(ctx, src, g.N, ctx->stage, &rc);
+  if (rc) return rc;
+  const bool dev = is_device_ptr(dst);
+  float* d = dev ? dst : ctx->stage + g.N;
+  launch_warp(g, s, direction == 0 ? ctx->u10 : ctx->u01, d, ctx->stream);
+  CK(cudaGetLastError());
+  if (!dev) return copy_out(ctx, dst, d, g.N * sizeof(float));
+  return LDDMM_OK;
+}
+
+int lddmm_transfer_labels(lddmm_ctx* ctx, const uint16_t* L0, uint16_t* dst) {
+  if (!ctx || !L0 || !dst) return fail(ctx, LDDMM_ERR_INVALID_ARG, "NULL argument");
+  int rc;
+  if (!ctx->maps_valid && (rc = refresh_maps(ctx, false))) return rc;
+  const Grid& g = ctx->levels[ctx->cur].g;
+  const uint16_t* s = L0;
+  uint16_t* st = reinterpret_cast<uint16_t*>(ctx->stage);
+  if (!is_device_ptr(L0)) {
+    CK(cudaMemcpyAsync(st, L0, g.N * sizeof(uint16_t), cudaMemcpyDefault, ctx->stream));
+    s = st;
+  }
+  const bool dev = is_device_ptr(dst);
+  uint16_t* d = dev ? dst : st + g.N;
+  launch_labels(g, s, ctx->u10, d, ctx->stream);
+  CK(cudaGetLastError());
+  if (!dev) return copy_out(ctx, dst, d, g.N * sizeof(uint16_t));
+  return LDDMM_OK;
+}
+
+int lddmm_get_velocity(lddmm_ctx* ctx, float* dst) {
+  if (!ctx || !dst) return fail(ctx, LDDMM_ERR_INVALID_ARG, "NULL argument");
+  const Grid& g = ctx->levels[ctx->cur].g;
+  return copy_out(ctx, dst, ctx->v, (size_t)ctx->p.T * 3 * g.N * sizeof(float));
+}
+
+int lddmm_set_velocity(lddmm_ctx* ctx, const float* src) {
+  if (!ctx || !src) return fail(ctx, LDDMM_ERR_INVALID_ARG, "NULL argument");
+  const Grid& g = ctx->levels[ctx->cur].g;
+  const int64_t n = (int64_t)ctx->p.T * 3 * g.N;
+  CK(cudaMemcpyAsync(ctx->v, src, n * sizeof(float), cudaMemcpyDefault, ctx->stream));
+  int rc = check_finite(ctx, ctx->v, n, "velocity");
+  if (rc) return rc;
+  ctx->maps_valid = false;
+  ctx->j0_valid = false;
+  ctx->last_E = -1.0;
+  return LDDMM_OK;
+}
+
+int lddmm_get_field(lddmm_ctx* ctx, int which, float* dst) {
+  if (!ctx || !dst) return fail(ctx, LDDMM_ERR_INVALID_ARG, "NULL argument");
+  const Level& L = ctx->levels[ctx->cur];
+  const int64_t N = L.g.N;
+  int rc;
+  switch (which) {
+    case LDDMM_FIELD_U10:
+    case LDDMM_FIELD_U01:
+    case LDDMM_FIELD_J0:
+      if (!ctx->maps_valid && (rc = refresh_maps(ctx, false))) return rc;
+      if (which == LDDMM_FIELD_U10) return copy_out(ctx, dst, ctx->u10, 3 * N * sizeof(float));
+      if (which == LDDMM_FIELD_U01) return copy_out(ctx, dst, ctx->u01, 3 * N * sizeof(float));
+      return copy_out(ctx, dst, ctx->J0T, N * sizeof(float));
+    case LDDMM_FIELD_I0: return copy_out(ctx, dst, L.I0, N * sizeof(float));
+    case LDDMM_FIELD_I1: return copy_out(ctx, dst, L.I1, N * sizeof(float));
+    case LDDMM_FIELD_M: return copy_out(ctx, dst, L.M, N * sizeof(float));
+    default: return fail(ctx, LDDMM_ERR_INVALID_ARG, "unknown field");
+  }
+}
+
+int lddmm_apply_K(lddmm_ctx* ctx, const float* src, float* dst) {
+  if (!ctx || !src || !dst) return fail(ctx, LDDMM_ERR_INVALID_ARG, "NULL argument");
+  const Level& L = ctx->levels[ctx->cur];
+  const int64_t N = L.g.N;
+  CK(cudaMemcpyAsync(ctx->stage, src, N * sizeof(float), cudaMemcpyDefault, ctx->stream));
+  CK(apply_K(L.kp, ctx->p.k_mode, ctx->stage, ctx->stage, ctx->work, 1, ctx->stream));
+  return copy_out(ctx, dst, ctx->stage, N * sizeof(float));
+}
+
+int lddmm_energy_eval(lddmm_ctx* ctx, lddmm_energy* out) {
+  if (!ctx || !out) return fail(ctx, LDDMM_ERR_INVALID_ARG, "NULL argument");
+  int rc = refresh_maps(ctx, true);
+  if (rc) return rc;
+  return read_energy(ctx, out, false);
+}
+
+int lddmm_dice(lddmm_ctx* ctx, const uint16_t* A, const uint16_t* B, int64_t n, double* out) {
+  if (!ctx || !A || !B || !out || n < 0) return fail(ctx, LDDMM_ERR_INVALID_ARG, "bad argument");
+  const uint16_t* a = A;
+  const uint16_t* b = B;
+  uint16_t* tmp = nullptr;
+  const bool da = is_device_ptr(A), db = is_device_ptr(B);
+  if (!da || !db) {
+    CK(cudaMalloc((void**)&tmp, (size_t)2 * n * sizeof(uint16_t) + 16));
+    if (!da) { CK(cudaMemcpyAsync(tmp, A, n * 2, cudaMemcpyDefault, ctx->stream)); a = tmp; }
+    if (!db) { CK(cudaMemcpyAsync(tmp + n, B, n * 2, cudaMemcpyDefault, ctx->stream)); b = tmp + n; }
+  }
+  CK(cudaMemsetAsync(ctx->hist, 0, 3 * 65536 * sizeof(unsigned long long), ctx->stream));
+  launch_dice_hist(a, b, n, ctx->hist, ctx->stream);
+  CK(cudaGetLastError());
+  std::vector<unsigned long long> h(3 * 65536);
+  CK(cudaMemcpyAsync(h.data(), ctx->hist, h.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = wait_stream(ctx);
+  if (tmp) cudaFree(tmp);
+  if (rc) return rc;
+  double s = 0.0;
+  int cnt = 0;
+  for (int l = 1; l < 65536; ++l) {
+    const unsigned long long na = h[l], nb = h[65536 + l], ni = h[2 * 65536 + l];
+    if (na + nb == 0) continue;
+    s += 2.0 * (double)ni / (double)(na + nb);
+    ++cnt;
+  }
+  *out = cnt ? s / cnt : 1.0;
+  return LDDMM_OK;
+}
+
+int lddmm_profile_start(lddmm_ctx* ctx, int max_launches) {
+  if (!ctx || max_launches < 1) return fail(ctx, LDDMM_ERR_INVALID_ARG, "bad argument");
+  for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+  ctx->prof_ev.assign(2 * (size_t)max_launches, nullptr);
+  for (auto& e : ctx->prof_ev) CK(cudaEventCreate(&e));
+  ctx->prof_kid.assign(max_launches, -1);
+  ctx->prof_used = 0;
+  ctx->prof_overflow = false;
+  ctx->prof_open = -1;
+  ctx->prof_on = true;
+  return LDDMM_OK;
+}
+
+int lddmm_profile_stop(lddmm_ctx* ctx, lddmm_kernel_stat* out, int max_out, int* n_out) {
+  if (!ctx) return fail(nullptr, LDDMM_ERR_INVALID_ARG, "ctx is NULL");
+  ctx->prof_on = false;
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  std::vector<double> tot(KID_COUNT, 0.0);
+  std::vector<int> cnt(KID_COUNT, 0);
+  for (size_t i = 0; i < ctx->prof_used; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]));
+    tot[ctx->prof_kid[i]] += ms;
+    cnt[ctx->prof_kid[i]] += 1;
+  }
+  int n = 0;
+  for (int k = 0; k < KID_COUNT; ++k) {
+    if (!cnt[k]) continue;
+    if (out && n < max_out) {
+      std::memset(&out[n], 0, sizeof(lddmm_kernel_stat));
+      std::strncpy(out[n].name, kernel_name(k), sizeof(out[n].name) - 1);
+      out[n].launches = cnt[k];
+      out[n].total_ms = tot[k];
+    }
+    ++n;
+  }
+  if (n_out) *n_out = n;
+  for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+  ctx->prof_ev.clear();
+  if (ctx->prof_overflow) return fail(ctx, LDDMM_ERR_STATE, "profile buffer overflowed (raise max_launches)");
+  return LDDMM_OK;
+}
+
+int lddmm_set_timeout(lddmm_ctx* ctx, float seconds) {
+  if (!ctx) return fail(nullptr, LDDMM_ERR_INVALID_ARG, "ctx is NULL");
+  ctx->p.timeout_s = seconds;
+  return LDDMM_OK;
+}
+
+const char* lddmm_last_error(lddmm_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_global_error.c_str();
+}
+
+void lddmm_destroy(lddmm_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+  release(ctx);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,300 @@
+"""Thin ctypes binding of liblddmm (include/lddmm.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; there is no CPU path.  Arrays may be
+``torch.Tensor`` (device or host, contiguous) or ``numpy.ndarray``; each is passed to the C
+ABI as a raw pointer and the library copies host memory itself (cudaMemcpyDefault).
+
+The functions keep the C names (``lddmm_create``, ``lddmm_step`` ...); :class:`Lddmm` is a
+small owner of one context on top of them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblddmm.so")
+
+LDDMM_OK = 0
+LDDMM_ERR_INVALID_ARG = -1
+LDDMM_ERR_OOM = -2
+LDDMM_ERR_CUDA = -3
+LDDMM_ERR_NONFINITE = -4
+LDDMM_ERR_STATE = -5
+LDDMM_ERR_TIMEOUT = -6
+
+LDDMM_K_FP32 = 0
+LDDMM_K_BF16X3 = 1
+LDDMM_K_BF16 = 2
+
+LDDMM_FIELD_U10 = 0
+LDDMM_FIELD_U01 = 1
+LDDMM_FIELD_J0 = 2
+LDDMM_FIELD_I0 = 3
+LDDMM_FIELD_I1 = 4
+LDDMM_FIELD_M = 5
+
+
+class lddmm_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("hx", ctypes.c_float), ("hy", ctypes.c_float), ("hz", ctypes.c_float),
+                ("T", ctypes.c_int),
+                ("alpha", ctypes.c_float), ("gamma", ctypes.c_float), ("sigma", ctypes.c_float),
+                ("epsilon", ctypes.c_float), ("iterations", ctypes.c_int),
+                ("num_levels", ctypes.c_int), ("level_factor", ctypes.c_int * 4),
+                ("k_mode", ctypes.c_int), ("flags", ctypes.c_int), ("timeout_s", ctypes.c_float)]
+
+
+class lddmm_energy(ctypes.Structure):
+    _fields_ = [("total", ctypes.c_double), ("reg", ctypes.c_double), ("data", ctypes.c_double),
+                ("min_det", ctypes.c_double), ("iter", ctypes.c_int), ("level", ctypes.c_int),
+                ("fold", ctypes.c_int), ("pad", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class lddmm_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int), ("pad", ctypes.c_int),
+                ("total_ms", ctypes.c_double)]
+
+
+class LddmmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("liblddmm error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "lddmm_default_params": (ctypes.c_int, [ctypes.POINTER(lddmm_params), ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "lddmm_create": (ctypes.c_int, [ctypes.POINTER(lddmm_params), _P, _P, _P, _P, ctypes.POINTER(_P)]),
+    "lddmm_set_images": (ctypes.c_int, [_P, _P, _P, _P]),
+    "lddmm_step": (ctypes.c_int, [_P, ctypes.POINTER(lddmm_energy)]),
+    "lddmm_register": (ctypes.c_int, [_P, ctypes.POINTER(lddmm_energy), ctypes.c_int]),
+    "lddmm_set_level": (ctypes.c_int, [_P, ctypes.c_int]),
+    "lddmm_grid": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "lddmm_warp": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "lddmm_transfer_labels": (ctypes.c_int, [_P, _P, _P]),
+    "lddmm_get_velocity": (ctypes.c_int, [_P, _P]),
+    "lddmm_set_velocity": (ctypes.c_int, [_P, _P]),
+    "lddmm_get_field": (ctypes.c_int, [_P, ctypes.c_int, _P]),
+    "lddmm_apply_K": (ctypes.c_int, [_P, _P, _P]),
+    "lddmm_energy_eval": (ctypes.c_int, [_P, ctypes.POINTER(lddmm_energy)]),
+    "lddmm_dice": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
+    "lddmm_set_timeout": (ctypes.c_int, [_P, ctypes.c_float]),
+    "lddmm_profile_start": (ctypes.c_int, [_P, ctypes.c_int]),
+    "lddmm_profile_stop": (ctypes.c_int, [_P, ctypes.POINTER(lddmm_kernel_stat), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int)]),
+    "lddmm_last_error": (ctypes.c_char_p, [_P]),
+    "lddmm_destroy": (None, [_P]),
+}
+
+
+def load(path: str | None = None):
+    """Load liblddmm.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError("liblddmm.so not built (%s); run __graft_entry__.build() or "
+                          "python -m paper_1605_02060_gb300.build" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor or numpy array (must be contiguous)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError("expected a torch.Tensor or numpy.ndarray, got %r" % type(a))
+
+
+def _check(rc, ctx=None):
+    if rc != LDDMM_OK:
+        msg = load().lddmm_last_error(ctx)
+        raise LddmmError(rc, msg.decode() if msg else "")
+
+
+def default_params(nx, ny, nz, **kw) -> lddmm_params:
+    p = lddmm_params()
+    _check(load().lddmm_default_params(ctypes.byref(p), nx, ny, nz))
+    for k, v in kw.items():
+        if k == "level_factor":
+            for i, f in enumerate(v):
+                p.level_factor[i] = int(f)
+            p.num_levels = len(v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Lddmm:
+    """One registration context (owns an ``lddmm_ctx``).
+
+    ``I0``, ``I1``, ``M``: float32 arrays of shape (nz, ny, nx); ``stream``: a
+    ``torch.cuda.Stream`` or raw handle (None: the library's own stream).
+    """
+
+    def __init__(self, params: lddmm_params, I0, I1, M=None, stream=None):
+        lib = load()
+        self._keep = (I0, I1, M)
+        s = None
+        if stream is not None:
+            s = ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+        ctx = ctypes.c_void_p()
+        rc = lib.lddmm_create(ctypes.byref(params), _ptr(I0), _ptr(I1), _ptr(M), s,
+                              ctypes.byref(ctx))
+        _check(rc, None)
+        self.ctx = ctx
+        self.params = params
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().lddmm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- calls ---------------------------------------------------------------------------------
+    def grid(self):
+        nx, ny, nz, lv = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().lddmm_grid(self.ctx, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(nz),
+                                 ctypes.byref(lv)), self.ctx)
+        return nx.value, ny.value, nz.value, lv.value
+
+    @property
+    def shape(self):
+        nx, ny, nz, _ = self.grid()
+        return (nz, ny, nx)
+
+    def step(self, want_energy=True):
+        e = lddmm_energy()
+        _check(load().lddmm_step(self.ctx, ctypes.byref(e) if want_energy else None), self.ctx)
+        return e.as_dict() if want_energy else None
+
+    def register(self):
+        n = self.params.num_levels * self.params.iterations
+        arr = (lddmm_energy * max(1, n))()
+        _check(load().lddmm_register(self.ctx, arr, n), self.ctx)
+        return [arr[i].as_dict() for i in range(n)]
+
+    def set_level(self, level):
+        _check(load().lddmm_set_level(self.ctx, level), self.ctx)
+
+    def set_images(self, I0, I1, M=None):
+        self._keep = (I0, I1, M)
+        _check(load().lddmm_set_images(self.ctx, _ptr(I0), _ptr(I1), _ptr(M)), self.ctx)
+
+    def energy(self):
+        e = lddmm_energy()
+        _check(load().lddmm_energy_eval(self.ctx, ctypes.byref(e)), self.ctx)
+        return e.as_dict()
+
+    def get_velocity(self, out=None):
+        if out is None:
+            out = np.empty((self.params.T, 3) + self.shape, np.float32)
+        _check(load().lddmm_get_velocity(self.ctx, _ptr(out)), self.ctx)
+        return out
+
+    def set_velocity(self, v):
+        _check(load().lddmm_set_velocity(self.ctx, _ptr(v)), self.ctx)
+
+    def get_field(self, which, out=None):
+        if out is None:
+            lead = (3,) if which in (LDDMM_FIELD_U10, LDDMM_FIELD_U01) else ()
+            out = np.empty(lead + self.shape, np.float32)
+        _check(load().lddmm_get_field(self.ctx, which, _ptr(out)), self.ctx)
+        return out
+
+    def warp(self, src, direction=0, out=None):
+        if out is None:
+            out = np.empty(self.shape, np.float32)
+        _check(load().lddmm_warp(self.ctx, _ptr(src), _ptr(out), direction), self.ctx)
+        return out
+
+    def transfer_labels(self, L0, out=None):
+        if out is None:
+            out = np.empty(self.shape, np.uint16)
+        _check(load().lddmm_transfer_labels(self.ctx, _ptr(L0), _ptr(out)), self.ctx)
+        return out
+
+    def apply_K(self, src, out=None):
+        if out is None:
+            out = np.empty(self.shape, np.float32)
+        _check(load().lddmm_apply_K(self.ctx, _ptr(src), _ptr(out)), self.ctx)
+        return out
+
+    def profile_start(self, max_launches):
+        _check(load().lddmm_profile_start(self.ctx, int(max_launches)), self.ctx)
+
+    def profile_stop(self):
+        """{kernel name: (launches, total device ms)} since profile_start."""
+        arr = (lddmm_kernel_stat * 64)()
+        n = ctypes.c_int()
+        _check(load().lddmm_profile_stop(self.ctx, arr, 64, ctypes.byref(n)), self.ctx)
+        return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(n.value)}
+
+    def set_timeout(self, seconds):
+        _check(load().lddmm_set_timeout(self.ctx, float(seconds)), self.ctx)
+
+    def dice(self, A, B):
+        d = ctypes.c_double()
+        n = int(np.prod(A.shape))
+        _check(load().lddmm_dice(self.ctx, _ptr(A), _ptr(B), n, ctypes.byref(d)), self.ctx)
+        return d.value
+
+
+# C-named module functions (same names as the ABI)
+def lddmm_create(params, I0, I1, M=None, stream=None):
+    return Lddmm(params, I0, I1, M, stream)
+
+
+def lddmm_step(ctx: Lddmm, want_energy=True):
+    return ctx.step(want_energy)
+
+
+def lddmm_register(ctx: Lddmm):
+    return ctx.register()
+
+
+def lddmm_warp(ctx: Lddmm, src, direction=0, out=None):
+    return ctx.warp(src, direction, out)
+
+
+def lddmm_transfer_labels(ctx: Lddmm, L0, out=None):
+    return ctx.transfer_labels(L0, out)
+
+
+def lddmm_destroy(ctx: Lddmm):
+    ctx.close()
