@@ -99,8 +99,10 @@ int lddmm_default_params(lddmm_params* p, int nx, int ny, int nz);
 
 /* Create a context: validates p, allocates device buffers for all levels, copies I0
  * (template), I1 (target) and M (weight mask, NULL = all ones; each nx*ny*nz float32) in,
- * builds the image pyramid and sets v = 0 at the coarsest level.  stream = cudaStream_t or NULL
- * (a private stream is created).  Returns LDDMM_ERR_NONFINITE if an input holds NaN/Inf. */
+ * builds the image pyramid and sets v = 0 at the coarsest level.  stream: the cudaStream_t all
+ * work of this context is enqueued on (NULL = the legacy default stream); device outputs are
+ * ready once that stream reaches the call's work.  Returns LDDMM_ERR_NONFINITE if an input holds
+ * NaN/Inf, LDDMM_ERR_CUDA if no GPU is usable. */
 int lddmm_create(const lddmm_params* p, const float* I0, const float* I1, const float* M,
                  void* stream, lddmm_ctx** out);
 

@@ -73,8 +73,10 @@ struct KPlan {
   float* Rx; float* Ry; float* Rz;
   // per-axis discrete-Laplacian eigenvalue of each row, lambda_d(row) / h_d^2 folded in
   float* lx; float* ly; float* lz;
-  // bf16 hi/lo splits of R for the tensor-core path (row-major, same shape)
-  uint16_t *Rx_hi, *Rx_lo, *Ry_hi, *Ry_lo, *Rz_hi, *Rz_lo;
+  // tensor-core operand tables per axis (x, y, z) and direction (0 forward, 1 inverse):
+  // nk = Npad/16 k-steps, each [hi | lo] bf16 blocks of Npad x 16 in K-major core-matrix order
+  uint16_t* tc[3][2];
+  int* err;  // device flag set by a tensor-core kernel whose bounded wait timed out
 };
 // Build device tables for one grid (allocates; free with kplan_destroy).
 cudaError_t kplan_create(KPlan* kp, int nx, int ny, int nz, float hx, float hy, float hz,
@@ -82,7 +84,13 @@ cudaError_t kplan_create(KPlan* kp, int nx, int ny, int nz, float hx, float hy, 
 void kplan_destroy(KPlan* kp);
 // out = K in for `ncomp` scalar fields stored back to back (each nx*ny*nz); work needs
 // ncomp*N floats.  in and out may alias.  mode: LDDMM_K_*.
+// If v_upd != nullptr the result is not stored: instead v_upd <- v_upd - eps (2 v_upd - K in)
+// (the gradient-descent update, fused into the last pass on the tensor-core path).
 cudaError_t apply_K(const KPlan& kp, int mode, const float* in, float* out, float* work,
-                    int ncomp, cudaStream_t s, const Hook& hook = Hook());
+                    int ncomp, cudaStream_t s, const Hook& hook = Hook(),
+                    float* v_upd = nullptr, float eps = 0.f);
+// One tensor-core axis pass (kernels_tc.cu): epi 0 plain, 1 times the K symbol, 2 update.
+cudaError_t tc_axis_pass(const KPlan& kp, int axis, bool inverse, int split, const float* in,
+                         float* out, int ncomp, int epi, float eps, cudaStream_t s);
 
 }  // namespace lddmm

@@ -51,6 +51,32 @@ static float bf16_to_f(uint16_t b) {
   return f;
 }
 
+// Tensor-core operand table: B(k, n) = R[n][k] (forward) or R[k][n] (inverse), zero-padded to
+// Npad = ceil16(n); per 16-wide k-step a bf16 hi block then a bf16 lo block (R = hi + lo), each
+// Npad rows x 16 k in the K-major no-swizzle core-matrix order the MMA descriptors expect:
+// element (row, kk) at byte (kk/8)*128 + (row/8)*256 + (row%8)*16 + (kk%8)*2.
+static void tc_table(const std::vector<float>& R, int n, bool inverse, std::vector<uint16_t>& t) {
+  const int Npad = (n + 15) / 16 * 16, nk = Npad / 16;
+  const size_t block = (size_t)Npad * 16;  // elements per hi (or lo) block
+  t.assign((size_t)nk * 2 * block, 0);
+  for (int s = 0; s < nk; ++s) {
+    uint16_t* hi = t.data() + (size_t)s * 2 * block;
+    uint16_t* lo = hi + block;
+    for (int row = 0; row < Npad; ++row)
+      for (int kk = 0; kk < 16; ++kk) {
+        const int k = s * 16 + kk;
+        float b = 0.f;
+        if (k < n && row < n) b = inverse ? R[(size_t)k * n + row] : R[(size_t)row * n + k];
+        const uint16_t bh = bf16_rn(b);
+        const uint16_t bl = bf16_rn(b - bf16_to_f(bh));
+        const size_t off = ((size_t)(kk / 8) * 128 + (size_t)(row / 8) * 256 + (row % 8) * 16 +
+                            (kk % 8) * 2) / 2;
+        hi[off] = bh;
+        lo[off] = bl;
+      }
+  }
+}
+
 template <typename T>
 static cudaError_t upload(T** dst, const std::vector<T>& src) {
   cudaError_t e = cudaMalloc((void**)dst, src.size() * sizeof(T));
@@ -67,30 +93,30 @@ cudaError_t kplan_create(KPlan* kp, int nx, int ny, int nz, float hx, float hy, 
   const double h[3] = {hx, hy, hz};
   float** Rs[3] = {&kp->Rx, &kp->Ry, &kp->Rz};
   float** ls[3] = {&kp->lx, &kp->ly, &kp->lz};
-  uint16_t** his[3] = {&kp->Rx_hi, &kp->Ry_hi, &kp->Rz_hi};
-  uint16_t** los[3] = {&kp->Rx_lo, &kp->Ry_lo, &kp->Rz_lo};
   for (int d = 0; d < 3; ++d) {
     std::vector<float> R, lam;
     real_dft_matrix(n[d], h[d], R, lam);
-    std::vector<uint16_t> hi(R.size()), lo(R.size());
-    for (size_t i = 0; i < R.size(); ++i) {
-      hi[i] = bf16_rn(R[i]);
-      lo[i] = bf16_rn(R[i] - bf16_to_f(hi[i]));
-    }
     cudaError_t e;
     if ((e = upload(Rs[d], R)) != cudaSuccess) return e;
     if ((e = upload(ls[d], lam)) != cudaSuccess) return e;
-    if ((e = upload(his[d], hi)) != cudaSuccess) return e;
-    if ((e = upload(los[d], lo)) != cudaSuccess) return e;
+    for (int dir = 0; dir < 2; ++dir) {
+      std::vector<uint16_t> t;
+      tc_table(R, n[d], dir == 1, t);
+      if ((e = upload(&kp->tc[d][dir], t)) != cudaSuccess) return e;
+    }
   }
-  return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)&kp->err, sizeof(int));
+  if (e != cudaSuccess) return e;
+  return cudaMemset(kp->err, 0, sizeof(int));
 }
 
 void kplan_destroy(KPlan* kp) {
-  void* ps[] = {kp->Rx, kp->Ry, kp->Rz, kp->lx, kp->ly, kp->lz,
-                kp->Rx_hi, kp->Rx_lo, kp->Ry_hi, kp->Ry_lo, kp->Rz_hi, kp->Rz_lo};
+  void* ps[] = {kp->Rx, kp->Ry, kp->Rz, kp->lx, kp->ly, kp->lz, kp->err};
   for (void* p : ps)
     if (p) cudaFree(p);
+  for (int d = 0; d < 3; ++d)
+    for (int dir = 0; dir < 2; ++dir)
+      if (kp->tc[d][dir]) cudaFree(kp->tc[d][dir]);
   *kp = KPlan{};
 }
 
@@ -234,11 +260,44 @@ static cudaError_t apply_K_fp32(const KPlan& kp, const float* in, float* out, fl
   return cudaGetLastError();
 }
 
+static cudaError_t apply_K_tc(const KPlan& kp, int split, const float* in, float* out,
+                              float* work, int ncomp, cudaStream_t s, const Hook& hook,
+                              float* v_upd, float eps) {
+  cudaError_t e;
+#define TC_PASS(kid, axis, inv, src, dst, epi)                                         \
+  do {                                                                                 \
+    hook(kid, 0);                                                                      \
+    e = tc_axis_pass(kp, axis, inv, split, src, dst, ncomp, epi, eps, s);              \
+    hook(kid, 1);                                                                      \
+    if (e != cudaSuccess) return e;                                                    \
+  } while (0)
+  TC_PASS(KID_KX_FWD, 0, false, in, work, 0);
+  TC_PASS(KID_KY_FWD, 1, false, work, out, 0);
+  TC_PASS(KID_KZ_SYM, 2, false, out, work, 1);
+  TC_PASS(KID_KZ_INV, 2, true, work, out, 0);
+  TC_PASS(KID_KY_INV, 1, true, out, work, 0);
+  if (v_upd) TC_PASS(KID_KX_INV, 0, true, work, v_upd, 2);
+  else TC_PASS(KID_KX_INV, 0, true, work, out, 0);
+#undef TC_PASS
+  return cudaSuccess;
+}
+
 cudaError_t apply_K(const KPlan& kp, int mode, const float* in, float* out, float* work,
-                    int ncomp, cudaStream_t s, const Hook& hook) {
+                    int ncomp, cudaStream_t s, const Hook& hook, float* v_upd, float eps) {
   switch (mode) {
-    case LDDMM_K_FP32:
-      return apply_K_fp32(kp, in, out, work, ncomp, s, hook);
+    case LDDMM_K_FP32: {
+      cudaError_t e = apply_K_fp32(kp, in, out, work, ncomp, s, hook);
+      if (e != cudaSuccess || !v_upd) return e;
+      Grid g{kp.nx, kp.ny, kp.nz, kp.nx * kp.ny * kp.nz};
+      hook(KID_UPDATE, 0);
+      launch_update(g, v_upd, out, eps, s);
+      hook(KID_UPDATE, 1);
+      return cudaGetLastError();
+    }
+    case LDDMM_K_BF16X3:
+      return apply_K_tc(kp, 1, in, out, work, ncomp, s, hook, v_upd, eps);
+    case LDDMM_K_BF16:
+      return apply_K_tc(kp, 0, in, out, work, ncomp, s, hook, v_upd, eps);
     default:
       return cudaErrorNotSupported;
   }

@@ -161,6 +161,9 @@ int validate(const lddmm_params* p, std::string& why) {
   }
   if (p->level_factor[p->num_levels - 1] != 1) { why = "the last level factor must be 1"; return LDDMM_ERR_INVALID_ARG; }
   if (p->k_mode < LDDMM_K_FP32 || p->k_mode > LDDMM_K_BF16) { why = "unknown k_mode"; return LDDMM_ERR_INVALID_ARG; }
+  if (p->k_mode != LDDMM_K_FP32 && (p->nx > 512 || p->ny > 512 || p->nz > 512)) {
+    why = "tensor-core K needs every axis <= 512 (TMEM columns)"; return LDDMM_ERR_INVALID_ARG;
+  }
   if (p->flags & ~1) { why = "unknown flag bits"; return LDDMM_ERR_INVALID_ARG; }
   return LDDMM_OK;
 }
@@ -247,10 +250,14 @@ double ordered_to_float(int i) {
 }
 
 int read_energy(lddmm_ctx* ctx, lddmm_energy* out, bool with_det) {
+  const Level& L = ctx->levels[ctx->cur];
   CK(cudaMemcpyAsync(ctx->acc_host, ctx->acc, sizeof(Acc), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&ctx->acc_host->nonfinite, L.kp.err, sizeof(int), cudaMemcpyDeviceToHost,
+                     ctx->stream));
   int rc = wait_stream(ctx);
   if (rc) return rc;
-  const Level& L = ctx->levels[ctx->cur];
+  if (ctx->acc_host->nonfinite)
+    return fail(ctx, LDDMM_ERR_CUDA, "a tensor-core pipeline wait timed out (results invalid)");
   const double h3 = (double)L.hx * L.hy * L.hz;
   const double s = ctx->p.sigma;
   out->reg = ctx->acc_host->e_reg * h3 / (double)ctx->p.T;
@@ -303,10 +310,8 @@ int run_step(lddmm_ctx* ctx) {
                     1.0f / (L.hx * L.hx), 1.0f / (L.hy * L.hy), 1.0f / (L.hz * L.hz), j == T - 1,
                     L.I0, L.I1, L.M, ctx->J0T, ctx->acc, s);
     hk(KID_FWD_FLOW, 1);
-    CK(apply_K(L.kp, ctx->p.k_mode, ctx->b, ctx->b, ctx->work, 3, s, hk));
-    hk(KID_UPDATE, 0);
-    launch_update(g, vj, ctx->b, ctx->eps, s);
-    hk(KID_UPDATE, 1);
+    // K b_j and the update v_j <- v_j - eps (2 v_j - K b_j)
+    CK(apply_K(L.kp, ctx->p.k_mode, ctx->b, ctx->b, ctx->work, 3, s, hk, vj, ctx->eps));
     uc = unx;
     pf ^= 1;
   }
@@ -447,14 +452,14 @@ int lddmm_create(const lddmm_params* p, const float* I0, const float* I1, const 
     delete ctx;
     return fail(nullptr, code, msg);
   };
-  if (stream) {
-    ctx->stream = (cudaStream_t)stream;
-  } else {
-    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
-      ctx->err = "could not create a CUDA stream (no usable GPU?)";
+  ctx->stream = (cudaStream_t)stream;  // NULL: the legacy default stream
+  {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->err = "no usable CUDA device";
       return bail(LDDMM_ERR_CUDA);
     }
-    ctx->own_stream = true;
   }
   const int nl = p->num_levels;
   ctx->levels.resize(nl);

@@ -153,12 +153,21 @@ class Lddmm:
     """One registration context (owns an ``lddmm_ctx``).
 
     ``I0``, ``I1``, ``M``: float32 arrays of shape (nz, ny, nx); ``stream``: a
-    ``torch.cuda.Stream`` or raw handle (None: the library's own stream).
+    ``torch.cuda.Stream`` or raw handle; None = torch's current stream when torch has CUDA
+    (so device tensors produced by torch are ordered with the library's work), else the
+    legacy default stream.
     """
 
     def __init__(self, params: lddmm_params, I0, I1, M=None, stream=None):
         lib = load()
         self._keep = (I0, I1, M)
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream()
+            except ImportError:
+                pass
         s = None
         if stream is not None:
             s = ctypes.c_void_p(getattr(stream, "cuda_stream", stream))

@@ -46,7 +46,7 @@ def _dev(a):
 
 
 K_MODES = {"fp32": (0, 1e-5), "bf16x3": (1, 2e-5)}
-MODES = ["fp32"]          # K implementations under test
+MODES = ["fp32", "bf16x3"]     # K implementations under test
 PROD = K_MODES[MODES[-1]][0]   # the mode the benchmark runs
 
 
@@ -68,6 +68,20 @@ def test_K_matches_oracle(L, O, mode, shape, h, alpha, gamma):
         got = ctx.apply_K(_dev(f))
     ref = O.apply_K(f, alpha, gamma, h)
     assert _rel(got.cpu().numpy() if hasattr(got, "cpu") else got, ref) < tol
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (29, 20, 33), (228, 160, 264)])
+def test_K_plain_bf16_products(L, O, shape):
+    """Plain bf16 products (no split): the error of an 8-bit mantissa, ~1e-3 relative."""
+    rng = np.random.default_rng(2)
+    f = rng.standard_normal(shape).astype(np.float32)
+    Z, Y, X = shape
+    p = L.default_params(X, Y, Z, k_mode=2)
+    a = np.zeros(shape, np.float32)
+    with L.Lddmm(p, a, a) as ctx:
+        got = ctx.apply_K(_dev(f))
+    err = _rel(got, O.apply_K(f, 0.02, 1.0, (1, 1, 1), workers=-1))
+    assert 1e-5 < err < 1e-2
 
 
 def test_K_single_mode_full_size(L):
@@ -248,7 +262,8 @@ def test_host_and_device_pointers_agree(L, synth):
         va = a.get_velocity()
         vb = torch.empty((4, 3, 16, 16, 16), device="cuda")
         b.get_velocity(vb)
-    assert ea == eb
+    # the energies are FP64 sums with atomics (summation order varies); v is deterministic
+    np.testing.assert_allclose(ea, eb, rtol=1e-12)
     np.testing.assert_array_equal(va, vb.cpu().numpy())
 
 
@@ -287,4 +302,7 @@ def test_backtracking_never_increases_energy(L, synth):
     p = L.default_params(32, 32, 32, T=4, epsilon=0.05, flags=1, k_mode=PROD)
     with L.Lddmm(p, _dev(pair.I0), _dev(pair.I1), _dev(pair.M)) as ctx:
         E = [ctx.step()["total"] for _ in range(8)]
-    assert all(b <= a for a, b in zip(E, E[1:])), E
+    # a rejected step returns the energy of the restored field again (equal up to the FP64
+    # atomic summation order)
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(E, E[1:])), E
+    assert E[-1] < 0.5 * E[0]
