@@ -98,6 +98,28 @@ __device__ __forceinline__ void block_sum_atomic(double v, double* dst) {
   }
 }
 
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of per-thread float partials: FP32 within a warp (32 terms), FP64 across warps
+// and for the global accumulator (one atomicAdd per block).
+__device__ __forceinline__ void block_sum_f_atomic(float v, double* dst) {
+  __shared__ double redf[32];
+  v = warp_sum_f(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) redf[wid] = (double)v;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    double s = lane < nw ? redf[lane] : 0.0;
+    s = warp_sum(s);
+    if (lane == 0 && s != 0.0) atomicAdd(dst, s);
+  }
+}
+
 // Float min through an order-preserving int encoding (atomicMin on int).
 __device__ __forceinline__ int float_to_ordered(float f) {
   int i = __float_as_int(f);

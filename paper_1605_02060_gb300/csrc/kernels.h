@@ -89,6 +89,10 @@ void kplan_destroy(KPlan* kp);
 cudaError_t apply_K(const KPlan& kp, int mode, const float* in, float* out, float* work,
                     int ncomp, cudaStream_t s, const Hook& hook = Hook(),
                     float* v_upd = nullptr, float eps = 0.f);
+// Persistent warp-specialised TMA/tcgen05 pass (kernels_tma.cu) and its shape condition.
+bool tma_pass_supported(const KPlan& kp, int axis);
+cudaError_t tma_axis_pass(const KPlan& kp, int axis, bool inverse, int split, const float* in,
+                          float* out, int ncomp, int epi, float eps, cudaStream_t s);
 // One tensor-core axis pass (kernels_tc.cu): epi 0 plain, 1 times the K symbol, 2 update.
 cudaError_t tc_axis_pass(const KPlan& kp, int axis, bool inverse, int split, const float* in,
                          float* out, int ncomp, int epi, float eps, cudaStream_t s);

@@ -267,7 +267,9 @@ static cudaError_t apply_K_tc(const KPlan& kp, int split, const float* in, float
 #define TC_PASS(kid, axis, inv, src, dst, epi)                                         \
   do {                                                                                 \
     hook(kid, 0);                                                                      \
-    e = tc_axis_pass(kp, axis, inv, split, src, dst, ncomp, epi, eps, s);              \
+    e = tma_pass_supported(kp, axis)                                                   \
+            ? tma_axis_pass(kp, axis, inv, split, src, dst, ncomp, epi, eps, s)        \
+            : tc_axis_pass(kp, axis, inv, split, src, dst, ncomp, epi, eps, s);        \
     hook(kid, 1);                                                                      \
     if (e != cudaSuccess) return e;                                                    \
   } while (0)

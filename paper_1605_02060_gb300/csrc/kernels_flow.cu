@@ -175,7 +175,7 @@ __global__ void k_fwd_flow(Grid g, const float* __restrict__ vj, const float* __
                            const float* __restrict__ I0, const float* __restrict__ I1,
                            const float* __restrict__ M, float* __restrict__ J0T, Acc* acc) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  double ereg = 0.0, edata = 0.0;
+  float ereg = 0.f, edata = 0.f;
   if (idx < g.N) {
     int x, y, z;
     xyz_of(g, idx, x, y, z);
@@ -204,19 +204,19 @@ __global__ void k_fwd_flow(Grid g, const float* __restrict__ vj, const float* __
                         (__ldg(p + ym) - 2.f * vc[c] + __ldg(p + yp)) * ihy2 +
                         (__ldg(p + zm) - 2.f * vc[c] + __ldg(p + zp)) * ihz2;
       const float Lv = gamma * vc[c] - alpha * lap;
-      ereg += (double)Lv * (double)Lv;
+      ereg = fmaf(Lv, Lv, ereg);
     }
     if (last) {
       const float j0 = tri_sample(I0, g, (float)x + ox, (float)y + oy, (float)z + oz);
       J0T[idx] = j0;
-      const double r = (double)j0 - (double)I1[idx];
-      edata = (double)M[idx] * r * r;
+      const float r = j0 - I1[idx];
+      edata = M[idx] * r * r;
     }
   }
-  block_sum_atomic(ereg, &acc->e_reg);
+  block_sum_f_atomic(ereg, &acc->e_reg);
   if (last) {
     __syncthreads();
-    block_sum_atomic(edata, &acc->e_data);
+    block_sum_f_atomic(edata, &acc->e_data);
   }
 }
 
