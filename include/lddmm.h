@@ -161,6 +161,20 @@ int lddmm_profile_start(lddmm_ctx* ctx, int max_launches);
  * *n_out = number of distinct kernels seen.  LDDMM_ERR_STATE if max_launches was too small. */
 int lddmm_profile_stop(lddmm_ctx* ctx, lddmm_kernel_stat* out, int max_out, int* n_out);
 
+/* The paper has no counterpart of this entry point.  dst = K src (K = (gamma - alpha Lap_h)^-2,
+ * FP32 per-axis real-DFT products, the same arithmetic as lddmm_apply_K with LDDMM_K_FP32) for
+ * one scalar field of nx*ny*nz float32 on a grid of spacing (hx, hy, hz), enqueued on `stream`
+ * (NULL = legacy default stream), WITHOUT allocating: for callers that cannot call cudaMalloc
+ * (inside stream capture, host callbacks, processes whose memory is reserved by another pool).
+ * Scratch is one file-scope device array (~11.5 MB, held by every GPU that loads the library until
+ * exit).  Limits: nx*ny*nz <= 2^21, each axis in [2, 512]; larger grids give
+ * LDDMM_ERR_INVALID_ARG.  src and dst must be device pointers (LDDMM_ERR_INVALID_ARG otherwise);
+ * dst may equal src.  All calls share the array: calls that overlap on the GPU race, so issue them
+ * on one stream.  The first call on a device looks up the array's address with that device
+ * current; make it before any stream capture.  Returns LDDMM_ERR_CUDA on a CUDA failure. */
+int lddmm_apply_K_noalloc(const float* src, float* dst, int nx, int ny, int nz, float hx,
+                          float hy, float hz, float alpha, float gamma, void* stream);
+
 /* Change the bound on host waits for this context (seconds, <= 0: 600 s). */
 int lddmm_set_timeout(lddmm_ctx* ctx, float seconds);
 

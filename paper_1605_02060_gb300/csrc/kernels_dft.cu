@@ -37,6 +37,10 @@ static void real_dft_matrix(int n, double h, std::vector<float>& R, std::vector<
   }
 }
 
+void host_real_dft_tables(int n, double h, std::vector<float>& R, std::vector<float>& lam) {
+  real_dft_matrix(n, h, R, lam);
+}
+
 static uint16_t bf16_rn(float f) {
   uint32_t u;
   std::memcpy(&u, &f, 4);

@@ -89,6 +89,9 @@ _SIGS = {
     "lddmm_energy_eval": (ctypes.c_int, [_P, ctypes.POINTER(lddmm_energy)]),
     "lddmm_dice": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
     "lddmm_set_timeout": (ctypes.c_int, [_P, ctypes.c_float]),
+    "lddmm_apply_K_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                             ctypes.c_float, ctypes.c_float, _P]),
     "lddmm_profile_start": (ctypes.c_int, [_P, ctypes.c_int]),
     "lddmm_profile_stop": (ctypes.c_int, [_P, ctypes.POINTER(lddmm_kernel_stat), ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int)]),
@@ -282,6 +285,22 @@ class Lddmm:
         n = int(np.prod(A.shape))
         _check(load().lddmm_dice(self.ctx, _ptr(A), _ptr(B), n, ctypes.byref(d)), self.ctx)
         return d.value
+
+
+def lddmm_apply_K_noalloc(src, dst, h=(1.0, 1.0, 1.0), alpha=0.02, gamma=1.0, stream=None):
+    """K src -> dst for device float32 tensors of shape (nz, ny, nx) without any GPU allocation
+    (scratch lives in a fixed static device array; see include/lddmm.h for the limits)."""
+    nz, ny, nx = src.shape
+    if stream is None:
+        try:
+            import torch
+            stream = torch.cuda.current_stream() if torch.cuda.is_available() else None
+        except ImportError:
+            stream = None
+    s = None if stream is None else ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+    _check(load().lddmm_apply_K_noalloc(_ptr(src), _ptr(dst), nx, ny, nz, h[0], h[1], h[2],
+                                        alpha, gamma, s))
+    return dst
 
 
 # C-named module functions (same names as the ABI)
