@@ -71,6 +71,11 @@ __device__ __forceinline__ void fd_stencil(int i, int n, int stride, int& lo, in
   else { lo = -stride; hi = stride; inv = 0.5f; }
 }
 
+// Linear thread index within the block (warps are 32 consecutive linear indices).
+__device__ __forceinline__ int linear_tid() {
+  return (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -87,11 +92,11 @@ __device__ __forceinline__ float warp_min(float v) {
 __device__ __forceinline__ void block_sum_atomic(double v, double* dst) {
   __shared__ double red[32];
   v = warp_sum(v);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lt = linear_tid(), lane = lt & 31, wid = lt >> 5;
   if (lane == 0) red[wid] = v;
   __syncthreads();
   if (wid == 0) {
-    const int nw = blockDim.x >> 5;
+    const int nw = (blockDim.x * blockDim.y * blockDim.z) >> 5;
     double s = lane < nw ? red[lane] : 0.0;
     s = warp_sum(s);
     if (lane == 0 && s != 0.0) atomicAdd(dst, s);
@@ -109,11 +114,11 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 __device__ __forceinline__ void block_sum_f_atomic(float v, double* dst) {
   __shared__ double redf[32];
   v = warp_sum_f(v);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lt = linear_tid(), lane = lt & 31, wid = lt >> 5;
   if (lane == 0) redf[wid] = (double)v;
   __syncthreads();
   if (wid == 0) {
-    const int nw = blockDim.x >> 5;
+    const int nw = (blockDim.x * blockDim.y * blockDim.z) >> 5;
     double s = lane < nw ? redf[lane] : 0.0;
     s = warp_sum(s);
     if (lane == 0 && s != 0.0) atomicAdd(dst, s);
@@ -129,11 +134,11 @@ __device__ __forceinline__ int float_to_ordered(float f) {
 __device__ __forceinline__ void block_min_atomic(float v, int* dst) {
   __shared__ float redm[32];
   v = warp_min(v);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int lt = linear_tid(), lane = lt & 31, wid = lt >> 5;
   if (lane == 0) redm[wid] = v;
   __syncthreads();
   if (wid == 0) {
-    const int nw = blockDim.x >> 5;
+    const int nw = (blockDim.x * blockDim.y * blockDim.z) >> 5;
     float s = lane < nw ? redm[lane] : 3.0e38f;
     s = warp_min(s);
     if (lane == 0) atomicMin(dst, float_to_ordered(s));

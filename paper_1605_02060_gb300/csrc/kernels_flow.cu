@@ -16,21 +16,25 @@ namespace lddmm {
 
 static inline int nblocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
-__device__ __forceinline__ void xyz_of(const Grid& g, int idx, int& x, int& y, int& z) {
-  x = idx % g.nx;
-  int r = idx / g.nx;
-  y = r % g.ny;
-  z = r / g.ny;
+// Voxel of this thread for a (32, 8) block on a (ceil(nx/32), ceil(ny/8), nz) grid: no integer
+// division per voxel.  Returns false for threads past the x/y extent.
+__device__ __forceinline__ bool voxel3d(const Grid& g, int& x, int& y, int& z, int& idx) {
+  x = blockIdx.x * 32 + threadIdx.x;
+  y = blockIdx.y * 8 + threadIdx.y;
+  z = blockIdx.z;
+  idx = (z * g.ny + y) * g.nx + x;
+  return x < g.nx && y < g.ny;
 }
+
+static inline dim3 grid3d(const Grid& g) { return dim3((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz); }
+static const dim3 kBlock3d(32, 8, 1);
 
 // --------------------------------------------------------------------------------------------
 // Backward sweep, part 1: displacement of phi_{j,1}.
 __global__ void k_back_disp(Grid g, const float* __restrict__ vj, const float* __restrict__ un,
                             float* __restrict__ uc, float dtx, float dty, float dtz) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= g.N) return;
-  int x, y, z;
-  xyz_of(g, idx, x, y, z);
+  int x, y, z, idx;
+  if (!voxel3d(g, x, y, z, idx)) return;
   const float dx = dtx * vj[idx], dy = dty * vj[g.N + idx], dz = dtz * vj[2 * g.N + idx];
   float ox = dx, oy = dy, oz = dz;
   if (un) {
@@ -69,11 +73,10 @@ __device__ __forceinline__ float jac_det(const Grid& g, const float* __restrict_
 __global__ void k_back_terms(Grid g, const float* __restrict__ uc, const float* __restrict__ I1,
                              const float* __restrict__ M, float* __restrict__ J1j,
                              float* __restrict__ Wj, Acc* acc) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int x, y, z, idx;
+  const bool in = voxel3d(g, x, y, z, idx);
   float dmin = 3.0e38f;
-  if (idx < g.N) {
-    int x, y, z;
-    xyz_of(g, idx, x, y, z);
+  if (in) {
     const float det = jac_det(g, uc, idx, x, y, z);
     Tri w = tri_setup(g, (float)x + uc[idx], (float)y + uc[g.N + idx], (float)z + uc[2 * g.N + idx]);
     J1j[idx] = tri_apply(I1, w);
@@ -88,17 +91,17 @@ void launch_flow_back(const Grid& g, const float* vj, const float* u_next, float
                       float dty, float dtz, Acc* acc, cudaStream_t s, const Hook& hook) {
   const int t = 256;
   hook(KID_BACK_DISP, 0);
-  k_back_disp<<<nblocks(g.N, t), t, 0, s>>>(g, vj, u_next, u_cur, dtx, dty, dtz);
+  k_back_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, vj, u_next, u_cur, dtx, dty, dtz);
   hook(KID_BACK_DISP, 1);
   hook(KID_BACK_TERMS, 0);
-  k_back_terms<<<nblocks(g.N, t), t, 0, s>>>(g, u_cur, I1, M, J1j, Wj, acc);
+  k_back_terms<<<grid3d(g), kBlock3d, 0, s>>>(g, u_cur, I1, M, J1j, Wj, acc);
   hook(KID_BACK_TERMS, 1);
 }
 
 void launch_flow_only_back(const Grid& g, const float* vj, const float* u_next, float* u_cur,
                            float dtx, float dty, float dtz, cudaStream_t s) {
   const int t = 256;
-  k_back_disp<<<nblocks(g.N, t), t, 0, s>>>(g, vj, u_next, u_cur, dtx, dty, dtz);
+  k_back_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, vj, u_next, u_cur, dtx, dty, dtz);
 }
 
 // --------------------------------------------------------------------------------------------
@@ -115,13 +118,11 @@ __device__ __forceinline__ float J0_at(const Grid& g, const float* __restrict__ 
 __global__ void k_fwd_terms(Grid g, const float* __restrict__ uc, const float* __restrict__ I0,
                             const float* __restrict__ J1j, const float* __restrict__ Wj,
                             float* __restrict__ b, float c, float ihx, float ihy, float ihz) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= g.N) return;
+  int x, y, z, idx;
+  if (!voxel3d(g, x, y, z, idx)) return;
   const float w = Wj[idx];
   float bx = 0.f, by = 0.f, bz = 0.f;
   if (w != 0.0f) {
-    int x, y, z;
-    xyz_of(g, idx, x, y, z);
     float j0;
     if (uc) j0 = J0_at(g, uc, I0, idx, x, y, z);
     else j0 = __ldg(I0 + idx);
@@ -164,7 +165,7 @@ void launch_fwd_terms(const Grid& g, const float* u_cur, const float* I0, const 
                       const float* Wj, float* b, float c, float ihx, float ihy, float ihz,
                       cudaStream_t s) {
   const int t = 256;
-  k_fwd_terms<<<nblocks(g.N, t), t, 0, s>>>(g, u_cur, I0, J1j, Wj, b, c, ihx, ihy, ihz);
+  k_fwd_terms<<<grid3d(g), kBlock3d, 0, s>>>(g, u_cur, I0, J1j, Wj, b, c, ihx, ihy, ihz);
 }
 
 // Forward sweep, flow: u_next = -dt v_j/h + u_cur(x - dt v_j/h); E_reg of v_j (periodic
@@ -174,11 +175,10 @@ __global__ void k_fwd_flow(Grid g, const float* __restrict__ vj, const float* __
                            float gamma, float ihx2, float ihy2, float ihz2, int last,
                            const float* __restrict__ I0, const float* __restrict__ I1,
                            const float* __restrict__ M, float* __restrict__ J0T, Acc* acc) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int x, y, z, idx;
+  const bool in = voxel3d(g, x, y, z, idx);
   float ereg = 0.f, edata = 0.f;
-  if (idx < g.N) {
-    int x, y, z;
-    xyz_of(g, idx, x, y, z);
+  if (in) {
     const float v0 = vj[idx], v1 = vj[g.N + idx], v2 = vj[2 * g.N + idx];
     const float dx = dtx * v0, dy = dty * v1, dz = dtz * v2;
     float ox = -dx, oy = -dy, oz = -dz;
@@ -225,16 +225,14 @@ void launch_fwd_flow(const Grid& g, const float* vj, const float* u_cur, float* 
                      float ihy2, float ihz2, bool last, const float* I0, const float* I1,
                      const float* M, float* J0T, Acc* acc, cudaStream_t s) {
   const int t = 256;
-  k_fwd_flow<<<nblocks(g.N, t), t, 0, s>>>(g, vj, u_cur, u_next, dtx, dty, dtz, alpha, gamma,
+  k_fwd_flow<<<grid3d(g), kBlock3d, 0, s>>>(g, vj, u_cur, u_next, dtx, dty, dtz, alpha, gamma,
                                            ihx2, ihy2, ihz2, last ? 1 : 0, I0, I1, M, J0T, acc);
 }
 
 __global__ void k_fwd_disp(Grid g, const float* __restrict__ vj, const float* __restrict__ uc,
                            float* __restrict__ un, float dtx, float dty, float dtz) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= g.N) return;
-  int x, y, z;
-  xyz_of(g, idx, x, y, z);
+  int x, y, z, idx;
+  if (!voxel3d(g, x, y, z, idx)) return;
   const float dx = dtx * vj[idx], dy = dty * vj[g.N + idx], dz = dtz * vj[2 * g.N + idx];
   float ox = -dx, oy = -dy, oz = -dz;
   if (uc) {
@@ -251,7 +249,7 @@ __global__ void k_fwd_disp(Grid g, const float* __restrict__ vj, const float* __
 void launch_flow_only_fwd(const Grid& g, const float* vj, const float* u_cur, float* u_next,
                           float dtx, float dty, float dtz, cudaStream_t s) {
   const int t = 256;
-  k_fwd_disp<<<nblocks(g.N, t), t, 0, s>>>(g, vj, u_cur, u_next, dtx, dty, dtz);
+  k_fwd_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, vj, u_cur, u_next, dtx, dty, dtz);
 }
 
 // --------------------------------------------------------------------------------------------
@@ -300,16 +298,14 @@ void launch_update(const Grid& g, float* vj, const float* Kb, float eps, cudaStr
 // Warp (trilinear pull-back) and label transfer (nearest neighbour, float32 rounding rule).
 __global__ void k_warp(Grid g, const float* __restrict__ src, const float* __restrict__ u,
                        float* __restrict__ dst) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= g.N) return;
-  int x, y, z;
-  xyz_of(g, idx, x, y, z);
+  int x, y, z, idx;
+  if (!voxel3d(g, x, y, z, idx)) return;
   dst[idx] = tri_sample(src, g, (float)x + u[idx], (float)y + u[g.N + idx], (float)z + u[2 * g.N + idx]);
 }
 
 void launch_warp(const Grid& g, const float* src, const float* u, float* dst, cudaStream_t s) {
   const int t = 256;
-  k_warp<<<nblocks(g.N, t), t, 0, s>>>(g, src, u, dst);
+  k_warp<<<grid3d(g), kBlock3d, 0, s>>>(g, src, u, dst);
 }
 
 __device__ __forceinline__ int nn_index(float i, float u, int n) {
@@ -321,10 +317,8 @@ __device__ __forceinline__ int nn_index(float i, float u, int n) {
 
 __global__ void k_labels(Grid g, const uint16_t* __restrict__ L0, const float* __restrict__ u,
                          uint16_t* __restrict__ dst) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= g.N) return;
-  int x, y, z;
-  xyz_of(g, idx, x, y, z);
+  int x, y, z, idx;
+  if (!voxel3d(g, x, y, z, idx)) return;
   const int ix = nn_index((float)x, u[idx], g.nx);
   const int iy = nn_index((float)y, u[g.N + idx], g.ny);
   const int iz = nn_index((float)z, u[2 * g.N + idx], g.nz);
@@ -334,17 +328,15 @@ __global__ void k_labels(Grid g, const uint16_t* __restrict__ L0, const float* _
 void launch_labels(const Grid& g, const uint16_t* L0, const float* u, uint16_t* dst,
                    cudaStream_t s) {
   const int t = 256;
-  k_labels<<<nblocks(g.N, t), t, 0, s>>>(g, L0, u, dst);
+  k_labels<<<grid3d(g), kBlock3d, 0, s>>>(g, L0, u, dst);
 }
 
 // --------------------------------------------------------------------------------------------
 // Multiscale: block mean with edge replication; trilinear cell-centred upsampling.
 __global__ void k_downsample(Grid f, Grid c, int factor, const float* __restrict__ src,
                              float* __restrict__ dst) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= c.N) return;
-  int x, y, z;
-  xyz_of(c, idx, x, y, z);
+  int x, y, z, idx;
+  if (!voxel3d(c, x, y, z, idx)) return;
   double s = 0.0;
   for (int dz = 0; dz < factor; ++dz) {
     const int zz = min(z * factor + dz, f.nz - 1);
@@ -362,15 +354,13 @@ __global__ void k_downsample(Grid f, Grid c, int factor, const float* __restrict
 void launch_downsample(const Grid& fine, const Grid& coarse, int factor, const float* src,
                        float* dst, cudaStream_t s) {
   const int t = 256;
-  k_downsample<<<nblocks(coarse.N, t), t, 0, s>>>(fine, coarse, factor, src, dst);
+  k_downsample<<<grid3d(coarse), kBlock3d, 0, s>>>(fine, coarse, factor, src, dst);
 }
 
 __global__ void k_upsample(Grid c, Grid f, float ratio, const float* __restrict__ src,
                            float* __restrict__ dst, int nfields) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= f.N) return;
-  int x, y, z;
-  xyz_of(f, idx, x, y, z);
+  int x, y, z, idx;
+  if (!voxel3d(f, x, y, z, idx)) return;
   Tri w = tri_setup(c, ((float)x + 0.5f) * ratio - 0.5f, ((float)y + 0.5f) * ratio - 0.5f,
                     ((float)z + 0.5f) * ratio - 0.5f);
   for (int k = 0; k < nfields; ++k)
@@ -380,7 +370,7 @@ __global__ void k_upsample(Grid c, Grid f, float ratio, const float* __restrict_
 void launch_upsample(const Grid& coarse, const Grid& fine, float ratio, const float* src,
                      float* dst, int nfields, cudaStream_t s) {
   const int t = 256;
-  k_upsample<<<nblocks(fine.N, t), t, 0, s>>>(coarse, fine, ratio, src, dst, nfields);
+  k_upsample<<<grid3d(fine), kBlock3d, 0, s>>>(coarse, fine, ratio, src, dst, nfields);
 }
 
 // --------------------------------------------------------------------------------------------
