@@ -81,7 +81,8 @@ typedef struct {
   int num_levels;            /* 1..4                                                         */
   int level_factor[4];       /* coarse -> fine downsampling factors, last must be 1, e.g. 4,2,1 */
   int k_mode;                /* LDDMM_K_*                                                    */
-  int flags;                 /* bit 0: halve epsilon and retry when the energy increases     */
+  int flags;                 /* bit 0: halve epsilon and retry when the energy increases;
+                                bit 1: checkpoint the forward maps in lddmm_energy_grad       */
   float timeout_s;           /* bound on every host wait for the stream (<= 0: 600 s)        */
 } lddmm_params;
 
@@ -142,6 +143,15 @@ int lddmm_apply_K(lddmm_ctx* ctx, const float* src, float* dst);
 
 /* Energy of the current v without updating it. */
 int lddmm_energy_eval(lddmm_ctx* ctx, lddmm_energy* out);
+
+/* Exact Euclidean gradient of the discrete energy above with respect to v, by reverse-mode
+ * differentiation of the forward sweep (§2.4 energy; the adjoint of the trilinear interpolation
+ * is a scatter-add).  v: [T][3][nz][ny][nx] float32 of the current level (NULL = the context's
+ * current v; otherwise it becomes the current v); grad: same layout, written; E: energy of v.
+ * Forward maps are stored for all T+1 steps, or, with params.flags bit 1, kept every
+ * ceil(sqrt(T)) steps and recomputed per segment during the reverse sweep.  The scatter uses
+ * float atomics: results vary at FP32 rounding between runs. */
+int lddmm_energy_grad(lddmm_ctx* ctx, const float* v, float* grad, double* E);
 
 /* Mean Dice overlap over labels > 0 present in A or B (uint16, n voxels each). */
 int lddmm_dice(lddmm_ctx* ctx, const uint16_t* A, const uint16_t* B, int64_t n, double* out);

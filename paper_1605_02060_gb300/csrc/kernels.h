@@ -65,6 +65,15 @@ void launch_fill(float* a, int64_t n, float value, cudaStream_t s);
 void launch_dice_hist(const uint16_t* A, const uint16_t* B, int64_t n,
                       unsigned long long* hist /* 3 x 65536 */, cudaStream_t s);
 
+// ---- exact gradient of the discrete energy (kernels_adjoint.cu) ----
+void launch_adj_init(const Grid& g, const float* uT, const float* I0, const float* I1,
+                     const float* M, float* gT, float scale, cudaStream_t s);
+void launch_adj_step(const Grid& g, const float* vj, const float* uj, const float* gnext,
+                     float* gcur, float* gradj, float dtx, float dty, float dtz, cudaStream_t s);
+void launch_apply_L3(const Grid& g, const float* src, float* dst, float alpha, float gamma,
+                     float ihx2, float ihy2, float ihz2, float scale, bool accumulate,
+                     cudaStream_t s);
+
 // ---- smoothing operator K (kernels_dft.cu) ----
 struct KPlan {
   int nx, ny, nz;

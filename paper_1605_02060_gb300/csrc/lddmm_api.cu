@@ -69,6 +69,12 @@ struct lddmm_ctx {
   size_t prof_used = 0;
   bool prof_overflow = false;
   int prof_open = -1;
+  // exact-gradient path (allocated on first use)
+  float* uall = nullptr;    // stored forward maps u_0..u_T (or checkpoints)
+  float* gA = nullptr;      // dE/du_{j+1}
+  float* gB = nullptr;      // dE/du_j
+  float* seg = nullptr;     // recomputed segment of maps (checkpoint mode)
+  int uall_slots = 0, seg_slots = 0;
 };
 
 namespace {
@@ -164,7 +170,7 @@ int validate(const lddmm_params* p, std::string& why) {
   if (p->k_mode != LDDMM_K_FP32 && (p->nx > 512 || p->ny > 512 || p->nz > 512)) {
     why = "tensor-core K needs every axis <= 512 (TMEM columns)"; return LDDMM_ERR_INVALID_ARG;
   }
-  if (p->flags & ~1) { why = "unknown flag bits"; return LDDMM_ERR_INVALID_ARG; }
+  if (p->flags & ~3) { why = "unknown flag bits"; return LDDMM_ERR_INVALID_ARG; }
   return LDDMM_OK;
 }
 
@@ -225,6 +231,9 @@ void release(lddmm_ctx* ctx) {
     cudaFree(L.I0); cudaFree(L.I1); cudaFree(L.M);
     kplan_destroy(&L.kp);
   }
+  void* ps2[] = {ctx->uall, ctx->gA, ctx->gB, ctx->seg};
+  for (void* p : ps2)
+    if (p) cudaFree(p);
   void* ps[] = {ctx->v, ctx->v_tmp, ctx->v_prev, ctx->uB[0], ctx->uB[1], ctx->uF[0], ctx->uF[1], ctx->J1,
                 ctx->W, ctx->b, ctx->work, ctx->J0T, ctx->stage, ctx->acc, ctx->flag, ctx->hist};
   for (void* p : ps)
@@ -714,6 +723,106 @@ int lddmm_profile_stop(lddmm_ctx* ctx, lddmm_kernel_stat* out, int max_out, int*
   for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
   ctx->prof_ev.clear();
   if (ctx->prof_overflow) return fail(ctx, LDDMM_ERR_STATE, "profile buffer overflowed (raise max_launches)");
+  return LDDMM_OK;
+}
+
+int lddmm_energy_grad(lddmm_ctx* ctx, const float* v, float* grad, double* E) {
+  if (!ctx || !grad) return fail(ctx, LDDMM_ERR_INVALID_ARG, "NULL argument");
+  const Level& L = ctx->levels[ctx->cur];
+  const Grid& g = L.g;
+  const int T = ctx->p.T;
+  const int64_t N = g.N, F = 3 * N;
+  cudaStream_t s = ctx->stream;
+  int rc;
+  if (v && (rc = lddmm_set_velocity(ctx, v))) return rc;
+  // forward maps: all T+1, or checkpoints every c steps plus a recomputed segment of c
+  const bool ckpt = (ctx->p.flags & 2) != 0;
+  int c = 1;
+  while (c * c < T) ++c;
+  const int nslots = ckpt ? (T - 1) / c + 2 : T + 1;   // checkpoints u_0, u_c, ..., and u_T
+  if (ctx->uall_slots < nslots) {
+    if (ctx->uall) cudaFree(ctx->uall);
+    ctx->uall = nullptr;
+    ctx->uall_slots = 0;
+    CK(cudaMalloc((void**)&ctx->uall, (size_t)nslots * ctx->Nmax * 3 * sizeof(float)));
+    ctx->uall_slots = nslots;
+  }
+  if (ckpt && ctx->seg_slots < c) {
+    if (ctx->seg) cudaFree(ctx->seg);
+    ctx->seg = nullptr;
+    ctx->seg_slots = 0;
+    CK(cudaMalloc((void**)&ctx->seg, (size_t)c * ctx->Nmax * 3 * sizeof(float)));
+    ctx->seg_slots = c;
+  }
+  if (!ctx->gA) CK(cudaMalloc((void**)&ctx->gA, (size_t)ctx->Nmax * 3 * sizeof(float)));
+  if (!ctx->gB) CK(cudaMalloc((void**)&ctx->gB, (size_t)ctx->Nmax * 3 * sizeof(float)));
+  const float dtx = dtv(ctx, L.hx), dty = dtv(ctx, L.hy), dtz = dtv(ctx, L.hz);
+  const float ihx2 = 1.0f / (L.hx * L.hx), ihy2 = 1.0f / (L.hy * L.hy), ihz2 = 1.0f / (L.hz * L.hz);
+  auto slot_of = [&](int j) -> float* {   // storage of u_j when it is kept
+    if (!ckpt) return ctx->uall + (size_t)j * F;
+    if (j == T) return ctx->uall + (size_t)(nslots - 1) * F;
+    return ctx->uall + (size_t)(j / c) * F;
+  };
+  // forward sweep (energy, u_j kept or checkpointed)
+  if ((rc = reset_acc(ctx))) return rc;
+  CK(cudaMemsetAsync(slot_of(0), 0, F * sizeof(float), s));
+  const float* uc = nullptr;
+  int pf = 0;
+  for (int j = 0; j < T; ++j) {
+    const bool keep = !ckpt || j + 1 == T || (j + 1) % c == 0;
+    float* unx = keep ? slot_of(j + 1) : ctx->uF[pf];
+    launch_fwd_flow(g, ctx->v + (int64_t)j * F, uc, unx, dtx, dty, dtz, ctx->p.alpha,
+                    ctx->p.gamma, ihx2, ihy2, ihz2, j == T - 1, L.I0, L.I1, L.M, ctx->J0T,
+                    ctx->acc, s);
+    uc = unx;
+    if (!keep) pf ^= 1;
+  }
+  CK(cudaGetLastError());
+  const bool dev = is_device_ptr(grad);
+  float* gout = dev ? grad : ctx->v_tmp;
+  // reverse sweep
+  const double h3 = (double)L.hx * L.hy * L.hz;
+  const double sg = ctx->p.sigma;
+  float* gnext = ctx->gA;
+  float* gcur = ctx->gB;
+  launch_adj_init(g, slot_of(T), L.I0, L.I1, L.M, gnext, (float)(2.0 * h3 / (sg * sg)), s);
+  int seg_base = -1;
+  for (int j = T - 1; j >= 0; --j) {
+    const float* uj;
+    if (!ckpt) {
+      uj = slot_of(j);
+    } else {
+      const int k = (j / c) * c;
+      if (seg_base != k) {   // recompute u_k .. u_{min(k+c,T)-1} from the checkpoint u_k
+        CK(cudaMemcpyAsync(ctx->seg, slot_of(k), F * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        for (int i = 1; i < c && k + i < T; ++i)
+          launch_flow_only_fwd(g, ctx->v + (int64_t)(k + i - 1) * F, ctx->seg + (size_t)(i - 1) * F,
+                               ctx->seg + (size_t)i * F, dtx, dty, dtz, s);
+        seg_base = k;
+      }
+      uj = ctx->seg + (size_t)(j - k) * F;
+    }
+    float* gradj = gout + (int64_t)j * F;
+    if (j > 0) CK(cudaMemsetAsync(gcur, 0, F * sizeof(float), s));
+    launch_adj_step(g, ctx->v + (int64_t)j * F, j > 0 ? uj : nullptr, gnext, j > 0 ? gcur : nullptr,
+                    gradj, dtx, dty, dtz, s);
+    // regulariser: + 2 dt h^3 L(L v_j)
+    launch_apply_L3(g, ctx->v + (int64_t)j * F, ctx->work, ctx->p.alpha, ctx->p.gamma, ihx2, ihy2,
+                    ihz2, 1.0f, false, s);
+    launch_apply_L3(g, ctx->work, gradj, ctx->p.alpha, ctx->p.gamma, ihx2, ihy2, ihz2,
+                    (float)(2.0 * h3 / T), true, s);
+    std::swap(gnext, gcur);
+  }
+  CK(cudaGetLastError());
+  lddmm_energy e{};
+  if ((rc = read_energy(ctx, &e, false))) return rc;
+  if (E) *E = e.total;
+  if (!dev) {
+    CK(cudaMemcpyAsync(grad, gout, (size_t)T * F * sizeof(float), cudaMemcpyDefault, s));
+    if ((rc = wait_stream(ctx))) return rc;
+  }
+  ctx->maps_valid = false;
+  ctx->j0_valid = false;
   return LDDMM_OK;
 }
 

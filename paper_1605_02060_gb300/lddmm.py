@@ -88,6 +88,7 @@ _SIGS = {
     "lddmm_apply_K": (ctypes.c_int, [_P, _P, _P]),
     "lddmm_energy_eval": (ctypes.c_int, [_P, ctypes.POINTER(lddmm_energy)]),
     "lddmm_dice": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
+    "lddmm_energy_grad": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "lddmm_set_timeout": (ctypes.c_int, [_P, ctypes.c_float]),
     "lddmm_apply_K_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -279,6 +280,14 @@ class Lddmm:
 
     def set_timeout(self, seconds):
         _check(load().lddmm_set_timeout(self.ctx, float(seconds)), self.ctx)
+
+    def energy_grad(self, v=None, grad=None):
+        """(E, dE/dv) of the discrete energy, exact reverse mode on the GPU."""
+        if grad is None:
+            grad = np.empty((self.params.T, 3) + self.shape, np.float32)
+        E = ctypes.c_double()
+        _check(load().lddmm_energy_grad(self.ctx, _ptr(v), _ptr(grad), ctypes.byref(E)), self.ctx)
+        return E.value, grad
 
     def dice(self, A, B):
         d = ctypes.c_double()
