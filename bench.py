@@ -188,8 +188,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "masked LDDMM 264x160x228 T=10, brain-shaped "
-                                             "atlas/target mask pair (seed 1)", "l2": "n/a (CPU)"},
+            "data": "synthetic", "config": {"workload": "masked LDDMM %dx%dx%d T=10, brain-shaped atlas/target mask pair "
+                                             "(seed 1)" % (SHAPE[2], SHAPE[1], SHAPE[0]),
+                                 "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample + " per step; NumPy/SciPy FP64, one thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -297,8 +298,9 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "masked LDDMM 264x160x228 T=10, brain-shaped atlas/target mask "
-                                   "pair (seed 1), fp32 fields, K via %s DFT products" % kname,
+            "config": {"workload": "masked LDDMM %dx%dx%d T=10, brain-shaped atlas/target mask "
+                                   "pair (seed 1), fp32 fields, K via %s DFT products"
+                                   % (X, Y, Z, kname),
                        "grid": [X, Y, Z], "T": T, "alpha": 0.02, "gamma": 1.0, "sigma": 0.1,
                        "epsilon": 1e-3, "k_mode": kname,
                        "parallelism": "replicas" if ws > 1 else "single",
@@ -344,7 +346,15 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--kmode", type=int, default=None, help="0 fp32, 1 bf16x3, 2 bf16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, nargs=3, default=None, metavar=("X", "Y", "Z"),
+                    help="override the 264 160 228 grid (tests only; the metric is quoted on the "
+                         "default)")
     args = ap.parse_args()
+    global SHAPE, METRIC
+    if args.grid:
+        X, Y, Z = args.grid
+        SHAPE = (Z, Y, X)
+        METRIC = "LDDMM iters/s at %dx%dx%d T=10" % (X, Y, Z)
     if args.kmode is None:
         args.kmode = DEFAULT_KMODE
     if args.impl == "reference":
@@ -352,7 +362,7 @@ def main():
     return run_ours(args)
 
 
-DEFAULT_KMODE = 0
+DEFAULT_KMODE = 1   # tensor-core bf16x3 DFT products (FP32-accurate)
 
 if __name__ == "__main__":
     sys.exit(main())
