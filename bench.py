@@ -242,6 +242,9 @@ def run_ours(args):
     ms_max = max_over_ranks(ws, ms)
     value = ws * args.steps / (ms_max / 1000.0)
     e_last = ctx.energy()
+    extras = None
+    if ws == 1 and not args.no_extras:
+        extras = measure_extras(L, I0, I1, M, stream, dev)
     # end to end through the public API with host buffers: every step copies the images in from
     # pinned host memory and reads the energy back
     h0 = torch.from_numpy(pair.I0).pin_memory()
@@ -311,9 +314,60 @@ def run_ours(args):
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 3),
                             "share": round(v[1] / sum(x[1] for x in prof.values()), 4)}
                         for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
-            "energy_after": e_last["total"]}
+            "energy_after": e_last["total"], "extras": extras}
     print(json.dumps(line))
     return 0
+
+
+def _time_steps(L, params, I0, I1, M, stream, warm=2, steps=5):
+    import torch
+    ctx = L.Lddmm(params, I0, I1, M, stream=stream)
+    for _ in range(warm):
+        ctx.step(want_energy=False)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.step(want_energy=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ctx.close()
+    return steps / (e0.elapsed_time(e1) / 1000.0)
+
+
+def measure_extras(L, I0, I1, M, stream, dev):
+    """Secondary measurements reported beside the headline: the same iteration with the other
+    precision settings, and the exact-gradient (adjoint) evaluation on a 128^3 pair."""
+    import numpy as np
+    import torch
+
+    from paper_1605_02060_gb300 import synth
+    Z, Y, X = SHAPE
+    out = {}
+    for name, kw in (("bf16_storage_bf16x3_K", dict(k_mode=1, storage=1)),
+                     ("fp32_storage_bf16_K", dict(k_mode=2)),
+                     ("fp32_storage_fp32_K", dict(k_mode=0))):
+        p = L.default_params(X, Y, Z, T=T, **kw)
+        out[name + "_iters_per_s"] = round(_time_steps(L, p, I0, I1, M, stream), 2)
+    pair = synth.union_pair((128, 128, 128), seed=100, amplitude=5.0)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    for flags, name in ((0, "adjoint_128cubed_ms"), (2, "adjoint_128cubed_checkpointed_ms")):
+        p = L.default_params(128, 128, 128, T=T, flags=flags)
+        ctx = L.Lddmm(p, d(pair.I0), d(pair.I1), d(pair.M), stream=stream)
+        g = torch.empty((T, 3, 128, 128, 128), device=dev)
+        ctx.energy_grad(None, g)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            ctx.energy_grad(None, g)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = round(e0.elapsed_time(e1) / 3, 3)
+        ctx.close()
+    return out
 
 
 def ctypes_sizeof_energy():
@@ -346,6 +400,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--kmode", type=int, default=None, help="0 fp32, 1 bf16x3, 2 bf16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--grid", type=int, nargs=3, default=None, metavar=("X", "Y", "Z"),
                     help="override the 264 160 228 grid (tests only; the metric is quoted on the "
                          "default)")

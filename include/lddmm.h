@@ -84,6 +84,8 @@ typedef struct {
   int flags;                 /* bit 0: halve epsilon and retry when the energy increases;
                                 bit 1: checkpoint the forward maps in lddmm_energy_grad       */
   float timeout_s;           /* bound on every host wait for the stream (<= 0: 600 s)        */
+  int storage;               /* 0: v and images stored float32; 1: stored bf16 (FP32 arithmetic,
+                                FP64 reductions; the precision form)                          */
 } lddmm_params;
 
 /* Energy of the velocity field at the start of an iteration (§2.4), FP64 reductions. */

@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <cuda_bf16.h>
 
 namespace lddmm {
 
@@ -60,6 +61,28 @@ __device__ __forceinline__ float tri_apply(const float* __restrict__ f, const Tr
 __device__ __forceinline__ float tri_sample(const float* __restrict__ f, const Grid& g,
                                             float qx, float qy, float qz) {
   return tri_apply(f, tri_setup(g, qx, qy, qz));
+}
+
+// Storage-type-generic loads: fields may be stored as float or bf16; arithmetic is FP32.
+__device__ __forceinline__ float ldf(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+__device__ __forceinline__ void stf(float* p, float v) { *p = v; }
+__device__ __forceinline__ void stf(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+template <typename T>
+__device__ __forceinline__ float tri_apply_t(const T* __restrict__ f, const Tri& w) {
+  const T* p = f + w.base;
+  const float c000 = ldf(p), c001 = ldf(p + w.sx);
+  const float c010 = ldf(p + w.sy), c011 = ldf(p + w.sy + w.sx);
+  const float c100 = ldf(p + w.sz), c101 = ldf(p + w.sz + w.sx);
+  const float c110 = ldf(p + w.sz + w.sy), c111 = ldf(p + w.sz + w.sy + w.sx);
+  const float a00 = c000 + w.tx * (c001 - c000);
+  const float a01 = c010 + w.tx * (c011 - c010);
+  const float a10 = c100 + w.tx * (c101 - c100);
+  const float a11 = c110 + w.tx * (c111 - c110);
+  const float b0 = a00 + w.ty * (a01 - a00);
+  const float b1 = a10 + w.ty * (a11 - a10);
+  return b0 + w.tz * (b1 - b0);
 }
 
 // Neighbour offsets and divisor of the first-derivative stencil along one axis at index i:

@@ -31,35 +31,39 @@ enum KernelId {
 };
 
 // ---- flows (kernels_flow.cu) ----
+// Velocity fields and images (vj, I0, I1, M) are stored as float (st = 0) or bf16 (st = 1);
+// displacements, J1, W, b and all arithmetic are float.
 // Backward sweep step j: u_cur = dt v_j / h + u_next(x + dt v_j / h)  (u_next == nullptr: id),
 // then J1_j = I1 o phi, W_j = (M o phi) det(I + Du_cur), min det into acc.
-void launch_flow_back(const Grid& g, const float* vj, const float* u_next, float* u_cur,
-                      const float* I1, const float* M, float* J1j, float* Wj, float dtx,
-                      float dty, float dtz, Acc* acc, cudaStream_t s, const Hook& hook);
+void launch_flow_back(const Grid& g, const void* vj, const float* u_next, float* u_cur,
+                      const void* I1, const void* M, float* J1j, float* Wj, float dtx,
+                      float dty, float dtz, Acc* acc, cudaStream_t s, const Hook& hook, int st);
 // Forward sweep step j: b = c W_j (J0_j - J1_j) grad J0_j / h,  J0_j = I0 o (id + u_cur).
-void launch_fwd_terms(const Grid& g, const float* u_cur, const float* I0, const float* J1j,
+void launch_fwd_terms(const Grid& g, const float* u_cur, const void* I0, const float* J1j,
                       const float* Wj, float* b, float c, float ihx, float ihy, float ihz,
-                      cudaStream_t s);
+                      cudaStream_t s, int st);
 // Forward sweep step j: u_next = -dt v_j / h + u_cur(x - dt v_j / h) (u_cur == nullptr: id),
 // E_reg contribution of v_j; if last, J0_T = I0 o (id + u_next) and E_data.
-void launch_fwd_flow(const Grid& g, const float* vj, const float* u_cur, float* u_next,
+void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u_next,
                      float dtx, float dty, float dtz, float alpha, float gamma, float ihx2,
-                     float ihy2, float ihz2, bool last, const float* I0, const float* I1,
-                     const float* M, float* J0T, Acc* acc, cudaStream_t s);
+                     float ihy2, float ihz2, bool last, const void* I0, const void* I1,
+                     const void* M, float* J0T, Acc* acc, cudaStream_t s, int st);
 // v_j <- v_j - eps (2 v_j - Kb), 3 components.
-void launch_update(const Grid& g, float* vj, const float* Kb, float eps, cudaStream_t s);
-// Displacement of phi_{1,0} only (flows without the residual), used to refresh maps.
-void launch_flow_only_fwd(const Grid& g, const float* vj, const float* u_cur, float* u_next,
-                          float dtx, float dty, float dtz, cudaStream_t s);
-void launch_flow_only_back(const Grid& g, const float* vj, const float* u_next, float* u_cur,
-                           float dtx, float dty, float dtz, cudaStream_t s);
+void launch_update(const Grid& g, void* vj, const float* Kb, float eps, cudaStream_t s, int st);
+// Displacement of phi_{1,0} / phi_{0,1} only (flows without the residual), to refresh maps.
+void launch_flow_only_fwd(const Grid& g, const void* vj, const float* u_cur, float* u_next,
+                          float dtx, float dty, float dtz, cudaStream_t s, int st);
+void launch_flow_only_back(const Grid& g, const void* vj, const float* u_next, float* u_cur,
+                           float dtx, float dty, float dtz, cudaStream_t s, int st);
 void launch_warp(const Grid& g, const float* src, const float* u, float* dst, cudaStream_t s);
 void launch_labels(const Grid& g, const uint16_t* L0, const float* u, uint16_t* dst,
                    cudaStream_t s);
 void launch_downsample(const Grid& fine, const Grid& coarse, int factor, const float* src,
-                       float* dst, cudaStream_t s);
-void launch_upsample(const Grid& coarse, const Grid& fine, float ratio, const float* src,
-                     float* dst, int nfields, cudaStream_t s);
+                       void* dst, cudaStream_t s, int st);
+void launch_upsample(const Grid& coarse, const Grid& fine, float ratio, const void* src,
+                     void* dst, int nfields, cudaStream_t s, int st);
+void launch_to_storage(const float* src, void* dst, int64_t n, cudaStream_t s, int st);
+void launch_from_storage(const void* src, float* dst, int64_t n, cudaStream_t s, int st);
 void launch_check_finite(const float* a, int64_t n, int* flag, cudaStream_t s);
 void launch_fill(float* a, int64_t n, float value, cudaStream_t s);
 void launch_dice_hist(const uint16_t* A, const uint16_t* B, int64_t n,

@@ -296,7 +296,7 @@ cudaError_t apply_K(const KPlan& kp, int mode, const float* in, float* out, floa
       if (e != cudaSuccess || !v_upd) return e;
       Grid g{kp.nx, kp.ny, kp.nz, kp.nx * kp.ny * kp.nz};
       hook(KID_UPDATE, 0);
-      launch_update(g, v_upd, out, eps, s);
+      launch_update(g, v_upd, out, eps, s, 0);
       hook(KID_UPDATE, 1);
       return cudaGetLastError();
     }

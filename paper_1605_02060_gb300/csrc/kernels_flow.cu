@@ -8,16 +8,15 @@
 //                   phi_{j+1,0}(x) = phi_{j,0}(x - dt v_j(x));
 //   update          v_j <- v_j - eps (2 v_j - K b_j).
 // Maps are displacements u = phi - id in voxels; dt v / h converts a velocity to voxels.
-// All kernels stream their fields with coalesced loads along x; the trilinear gathers of the
-// displacement and the images hit L1/L2 because displacements are small and smooth.
+// The velocity field and the images are stored as ST = float or bf16 (the precision form);
+// every computation is FP32 and reductions are FP64.  Kernels run on (32, 8) blocks over a
+// (ceil(nx/32), ceil(ny/8), nz) grid: rows of x are coalesced and no voxel index is divided.
 #include "kernels.h"
 
 namespace lddmm {
 
 static inline int nblocks(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
-// Voxel of this thread for a (32, 8) block on a (ceil(nx/32), ceil(ny/8), nz) grid: no integer
-// division per voxel.  Returns false for threads past the x/y extent.
 __device__ __forceinline__ bool voxel3d(const Grid& g, int& x, int& y, int& z, int& idx) {
   x = blockIdx.x * 32 + threadIdx.x;
   y = blockIdx.y * 8 + threadIdx.y;
@@ -31,11 +30,13 @@ static const dim3 kBlock3d(32, 8, 1);
 
 // --------------------------------------------------------------------------------------------
 // Backward sweep, part 1: displacement of phi_{j,1}.
-__global__ void k_back_disp(Grid g, const float* __restrict__ vj, const float* __restrict__ un,
+template <typename ST>
+__global__ void k_back_disp(Grid g, const ST* __restrict__ vj, const float* __restrict__ un,
                             float* __restrict__ uc, float dtx, float dty, float dtz) {
   int x, y, z, idx;
   if (!voxel3d(g, x, y, z, idx)) return;
-  const float dx = dtx * vj[idx], dy = dty * vj[g.N + idx], dz = dtz * vj[2 * g.N + idx];
+  const float dx = dtx * ldf(vj + idx), dy = dty * ldf(vj + g.N + idx),
+              dz = dtz * ldf(vj + 2 * g.N + idx);
   float ox = dx, oy = dy, oz = dz;
   if (un) {
     Tri w = tri_setup(g, (float)x + dx, (float)y + dy, (float)z + dz);
@@ -70,8 +71,9 @@ __device__ __forceinline__ float jac_det(const Grid& g, const float* __restrict_
 }
 
 // Backward sweep, part 2: J1_j = I1 o phi_{j,1}, W_j = (M o phi_{j,1}) det D phi_{j,1}.
-__global__ void k_back_terms(Grid g, const float* __restrict__ uc, const float* __restrict__ I1,
-                             const float* __restrict__ M, float* __restrict__ J1j,
+template <typename ST>
+__global__ void k_back_terms(Grid g, const float* __restrict__ uc, const ST* __restrict__ I1,
+                             const ST* __restrict__ M, float* __restrict__ J1j,
                              float* __restrict__ Wj, Acc* acc) {
   int x, y, z, idx;
   const bool in = voxel3d(g, x, y, z, idx);
@@ -79,43 +81,49 @@ __global__ void k_back_terms(Grid g, const float* __restrict__ uc, const float* 
   if (in) {
     const float det = jac_det(g, uc, idx, x, y, z);
     Tri w = tri_setup(g, (float)x + uc[idx], (float)y + uc[g.N + idx], (float)z + uc[2 * g.N + idx]);
-    J1j[idx] = tri_apply(I1, w);
-    Wj[idx] = tri_apply(M, w) * det;
+    J1j[idx] = tri_apply_t(I1, w);
+    Wj[idx] = tri_apply_t(M, w) * det;
     dmin = det;
   }
   block_min_atomic(dmin, &acc->min_det_ord);
 }
 
-void launch_flow_back(const Grid& g, const float* vj, const float* u_next, float* u_cur,
-                      const float* I1, const float* M, float* J1j, float* Wj, float dtx,
-                      float dty, float dtz, Acc* acc, cudaStream_t s, const Hook& hook) {
-  const int t = 256;
+void launch_flow_back(const Grid& g, const void* vj, const float* u_next, float* u_cur,
+                      const void* I1, const void* M, float* J1j, float* Wj, float dtx,
+                      float dty, float dtz, Acc* acc, cudaStream_t s, const Hook& hook, int st) {
   hook(KID_BACK_DISP, 0);
-  k_back_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, vj, u_next, u_cur, dtx, dty, dtz);
+  if (st) k_back_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, (const __nv_bfloat16*)vj, u_next, u_cur, dtx, dty, dtz);
+  else k_back_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, (const float*)vj, u_next, u_cur, dtx, dty, dtz);
   hook(KID_BACK_DISP, 1);
   hook(KID_BACK_TERMS, 0);
-  k_back_terms<<<grid3d(g), kBlock3d, 0, s>>>(g, u_cur, I1, M, J1j, Wj, acc);
+  if (st)
+    k_back_terms<<<grid3d(g), kBlock3d, 0, s>>>(g, u_cur, (const __nv_bfloat16*)I1,
+                                                (const __nv_bfloat16*)M, J1j, Wj, acc);
+  else
+    k_back_terms<<<grid3d(g), kBlock3d, 0, s>>>(g, u_cur, (const float*)I1, (const float*)M, J1j,
+                                                Wj, acc);
   hook(KID_BACK_TERMS, 1);
 }
 
-void launch_flow_only_back(const Grid& g, const float* vj, const float* u_next, float* u_cur,
-                           float dtx, float dty, float dtz, cudaStream_t s) {
-  const int t = 256;
-  k_back_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, vj, u_next, u_cur, dtx, dty, dtz);
+void launch_flow_only_back(const Grid& g, const void* vj, const float* u_next, float* u_cur,
+                           float dtx, float dty, float dtz, cudaStream_t s, int st) {
+  if (st) k_back_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, (const __nv_bfloat16*)vj, u_next, u_cur, dtx, dty, dtz);
+  else k_back_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, (const float*)vj, u_next, u_cur, dtx, dty, dtz);
 }
 
 // --------------------------------------------------------------------------------------------
 // Forward sweep, residual: b_j = c W_j (J0_j - J1_j) grad J0_j / h.
 // grad J0_j needs J0_j at the stencil neighbours; each is one trilinear lookup of I0 at the
 // neighbour's own mapped position (phi_{j,0} is known at every grid point).
+template <typename ST>
 __device__ __forceinline__ float J0_at(const Grid& g, const float* __restrict__ u,
-                                       const float* __restrict__ I0, int idx, int x, int y,
-                                       int z) {
-  return tri_sample(I0, g, (float)x + __ldg(u + idx), (float)y + __ldg(u + g.N + idx),
-                    (float)z + __ldg(u + 2 * g.N + idx));
+                                       const ST* __restrict__ I0, int idx, int x, int y, int z) {
+  return tri_apply_t(I0, tri_setup(g, (float)x + __ldg(u + idx), (float)y + __ldg(u + g.N + idx),
+                                   (float)z + __ldg(u + 2 * g.N + idx)));
 }
 
-__global__ void k_fwd_terms(Grid g, const float* __restrict__ uc, const float* __restrict__ I0,
+template <typename ST>
+__global__ void k_fwd_terms(Grid g, const float* __restrict__ uc, const ST* __restrict__ I0,
                             const float* __restrict__ J1j, const float* __restrict__ Wj,
                             float* __restrict__ b, float c, float ihx, float ihy, float ihz) {
   int x, y, z, idx;
@@ -125,7 +133,7 @@ __global__ void k_fwd_terms(Grid g, const float* __restrict__ uc, const float* _
   if (w != 0.0f) {
     float j0;
     if (uc) j0 = J0_at(g, uc, I0, idx, x, y, z);
-    else j0 = __ldg(I0 + idx);
+    else j0 = ldf(I0 + idx);
     const float r = c * w * (j0 - J1j[idx]);
     if (r != 0.0f) {
       float gr[3];
@@ -146,8 +154,8 @@ __global__ void k_fwd_terms(Grid g, const float* __restrict__ uc, const float* _
           fh = (dh == 0) ? j0 : J0_at(g, uc, I0, idx + hi, ph[0], ph[1], ph[2]);
           fl = (dl == 0) ? j0 : J0_at(g, uc, I0, idx + lo, pl[0], pl[1], pl[2]);
         } else {
-          fh = __ldg(I0 + idx + hi);
-          fl = __ldg(I0 + idx + lo);
+          fh = ldf(I0 + idx + hi);
+          fl = ldf(I0 + idx + lo);
         }
         gr[e] = (fh - fl) * inv;
       }
@@ -161,25 +169,30 @@ __global__ void k_fwd_terms(Grid g, const float* __restrict__ uc, const float* _
   b[2 * g.N + idx] = bz;
 }
 
-void launch_fwd_terms(const Grid& g, const float* u_cur, const float* I0, const float* J1j,
+void launch_fwd_terms(const Grid& g, const float* u_cur, const void* I0, const float* J1j,
                       const float* Wj, float* b, float c, float ihx, float ihy, float ihz,
-                      cudaStream_t s) {
-  const int t = 256;
-  k_fwd_terms<<<grid3d(g), kBlock3d, 0, s>>>(g, u_cur, I0, J1j, Wj, b, c, ihx, ihy, ihz);
+                      cudaStream_t s, int st) {
+  if (st)
+    k_fwd_terms<<<grid3d(g), kBlock3d, 0, s>>>(g, u_cur, (const __nv_bfloat16*)I0, J1j, Wj, b, c,
+                                               ihx, ihy, ihz);
+  else
+    k_fwd_terms<<<grid3d(g), kBlock3d, 0, s>>>(g, u_cur, (const float*)I0, J1j, Wj, b, c, ihx, ihy,
+                                               ihz);
 }
 
 // Forward sweep, flow: u_next = -dt v_j/h + u_cur(x - dt v_j/h); E_reg of v_j (periodic
 // 7-point (gamma - alpha Lap_h) v_j, summed over components); at the last step J0_T and E_data.
-__global__ void k_fwd_flow(Grid g, const float* __restrict__ vj, const float* __restrict__ uc,
+template <typename ST>
+__global__ void k_fwd_flow(Grid g, const ST* __restrict__ vj, const float* __restrict__ uc,
                            float* __restrict__ un, float dtx, float dty, float dtz, float alpha,
                            float gamma, float ihx2, float ihy2, float ihz2, int last,
-                           const float* __restrict__ I0, const float* __restrict__ I1,
-                           const float* __restrict__ M, float* __restrict__ J0T, Acc* acc) {
+                           const ST* __restrict__ I0, const ST* __restrict__ I1,
+                           const ST* __restrict__ M, float* __restrict__ J0T, Acc* acc) {
   int x, y, z, idx;
   const bool in = voxel3d(g, x, y, z, idx);
   float ereg = 0.f, edata = 0.f;
   if (in) {
-    const float v0 = vj[idx], v1 = vj[g.N + idx], v2 = vj[2 * g.N + idx];
+    const float v0 = ldf(vj + idx), v1 = ldf(vj + g.N + idx), v2 = ldf(vj + 2 * g.N + idx);
     const float dx = dtx * v0, dy = dty * v1, dz = dtz * v2;
     float ox = -dx, oy = -dy, oz = -dz;
     if (uc) {
@@ -199,18 +212,18 @@ __global__ void k_fwd_flow(Grid g, const float* __restrict__ vj, const float* __
     const float vc[3] = {v0, v1, v2};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float* p = vj + c * g.N + idx;
-      const float lap = (__ldg(p + xm) - 2.f * vc[c] + __ldg(p + xp)) * ihx2 +
-                        (__ldg(p + ym) - 2.f * vc[c] + __ldg(p + yp)) * ihy2 +
-                        (__ldg(p + zm) - 2.f * vc[c] + __ldg(p + zp)) * ihz2;
+      const ST* p = vj + c * g.N + idx;
+      const float lap = (ldf(p + xm) - 2.f * vc[c] + ldf(p + xp)) * ihx2 +
+                        (ldf(p + ym) - 2.f * vc[c] + ldf(p + yp)) * ihy2 +
+                        (ldf(p + zm) - 2.f * vc[c] + ldf(p + zp)) * ihz2;
       const float Lv = gamma * vc[c] - alpha * lap;
       ereg = fmaf(Lv, Lv, ereg);
     }
     if (last) {
-      const float j0 = tri_sample(I0, g, (float)x + ox, (float)y + oy, (float)z + oz);
+      const float j0 = tri_apply_t(I0, tri_setup(g, (float)x + ox, (float)y + oy, (float)z + oz));
       J0T[idx] = j0;
-      const float r = j0 - I1[idx];
-      edata = M[idx] * r * r;
+      const float r = j0 - ldf(I1 + idx);
+      edata = ldf(M + idx) * r * r;
     }
   }
   block_sum_f_atomic(ereg, &acc->e_reg);
@@ -220,20 +233,29 @@ __global__ void k_fwd_flow(Grid g, const float* __restrict__ vj, const float* __
   }
 }
 
-void launch_fwd_flow(const Grid& g, const float* vj, const float* u_cur, float* u_next,
+void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u_next,
                      float dtx, float dty, float dtz, float alpha, float gamma, float ihx2,
-                     float ihy2, float ihz2, bool last, const float* I0, const float* I1,
-                     const float* M, float* J0T, Acc* acc, cudaStream_t s) {
-  const int t = 256;
-  k_fwd_flow<<<grid3d(g), kBlock3d, 0, s>>>(g, vj, u_cur, u_next, dtx, dty, dtz, alpha, gamma,
-                                           ihx2, ihy2, ihz2, last ? 1 : 0, I0, I1, M, J0T, acc);
+                     float ihy2, float ihz2, bool last, const void* I0, const void* I1,
+                     const void* M, float* J0T, Acc* acc, cudaStream_t s, int st) {
+  if (st)
+    k_fwd_flow<<<grid3d(g), kBlock3d, 0, s>>>(
+        g, (const __nv_bfloat16*)vj, u_cur, u_next, dtx, dty, dtz, alpha, gamma, ihx2, ihy2, ihz2,
+        last ? 1 : 0, (const __nv_bfloat16*)I0, (const __nv_bfloat16*)I1, (const __nv_bfloat16*)M,
+        J0T, acc);
+  else
+    k_fwd_flow<<<grid3d(g), kBlock3d, 0, s>>>(g, (const float*)vj, u_cur, u_next, dtx, dty, dtz,
+                                              alpha, gamma, ihx2, ihy2, ihz2, last ? 1 : 0,
+                                              (const float*)I0, (const float*)I1,
+                                              (const float*)M, J0T, acc);
 }
 
-__global__ void k_fwd_disp(Grid g, const float* __restrict__ vj, const float* __restrict__ uc,
+template <typename ST>
+__global__ void k_fwd_disp(Grid g, const ST* __restrict__ vj, const float* __restrict__ uc,
                            float* __restrict__ un, float dtx, float dty, float dtz) {
   int x, y, z, idx;
   if (!voxel3d(g, x, y, z, idx)) return;
-  const float dx = dtx * vj[idx], dy = dty * vj[g.N + idx], dz = dtz * vj[2 * g.N + idx];
+  const float dx = dtx * ldf(vj + idx), dy = dty * ldf(vj + g.N + idx),
+              dz = dtz * ldf(vj + 2 * g.N + idx);
   float ox = -dx, oy = -dy, oz = -dz;
   if (uc) {
     Tri w = tri_setup(g, (float)x - dx, (float)y - dy, (float)z - dz);
@@ -246,10 +268,10 @@ __global__ void k_fwd_disp(Grid g, const float* __restrict__ vj, const float* __
   un[2 * g.N + idx] = oz;
 }
 
-void launch_flow_only_fwd(const Grid& g, const float* vj, const float* u_cur, float* u_next,
-                          float dtx, float dty, float dtz, cudaStream_t s) {
-  const int t = 256;
-  k_fwd_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, vj, u_cur, u_next, dtx, dty, dtz);
+void launch_flow_only_fwd(const Grid& g, const void* vj, const float* u_cur, float* u_next,
+                          float dtx, float dty, float dtz, cudaStream_t s, int st) {
+  if (st) k_fwd_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, (const __nv_bfloat16*)vj, u_cur, u_next, dtx, dty, dtz);
+  else k_fwd_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, (const float*)vj, u_cur, u_next, dtx, dty, dtz);
 }
 
 // --------------------------------------------------------------------------------------------
@@ -274,15 +296,23 @@ __global__ void k_update(int n4, int n, float4* __restrict__ v, const float4* __
   }
 }
 
-__global__ void k_update_scalar(int n, float* __restrict__ v, const float* __restrict__ kb,
+template <typename ST>
+__global__ void k_update_scalar(int n, ST* __restrict__ v, const float* __restrict__ kb,
                                 float eps) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) v[i] -= eps * (2.f * v[i] - kb[i]);
+  if (i < n) {
+    const float a = ldf(v + i);
+    stf(v + i, a - eps * (2.f * a - kb[i]));
+  }
 }
 
-void launch_update(const Grid& g, float* vj, const float* Kb, float eps, cudaStream_t s) {
+void launch_update(const Grid& g, void* vj, const float* Kb, float eps, cudaStream_t s, int st) {
   const int n = 3 * g.N;
   const int t = 256;
+  if (st) {
+    k_update_scalar<<<nblocks(n, t), t, 0, s>>>(n, (__nv_bfloat16*)vj, Kb, eps);
+    return;
+  }
   // float4 streaming when both fields start on a 16-byte boundary (v_j does not when 3N is odd
   // and j is odd), scalar otherwise.
   if (((uintptr_t)vj & 15) == 0 && ((uintptr_t)Kb & 15) == 0) {
@@ -290,7 +320,7 @@ void launch_update(const Grid& g, float* vj, const float* Kb, float eps, cudaStr
     k_update<<<nblocks(n4 > 0 ? n4 : 1, t), t, 0, s>>>(n4, n, reinterpret_cast<float4*>(vj),
                                                        reinterpret_cast<const float4*>(Kb), eps);
   } else {
-    k_update_scalar<<<nblocks(n, t), t, 0, s>>>(n, vj, Kb, eps);
+    k_update_scalar<<<nblocks(n, t), t, 0, s>>>(n, (float*)vj, Kb, eps);
   }
 }
 
@@ -304,7 +334,6 @@ __global__ void k_warp(Grid g, const float* __restrict__ src, const float* __res
 }
 
 void launch_warp(const Grid& g, const float* src, const float* u, float* dst, cudaStream_t s) {
-  const int t = 256;
   k_warp<<<grid3d(g), kBlock3d, 0, s>>>(g, src, u, dst);
 }
 
@@ -327,14 +356,14 @@ __global__ void k_labels(Grid g, const uint16_t* __restrict__ L0, const float* _
 
 void launch_labels(const Grid& g, const uint16_t* L0, const float* u, uint16_t* dst,
                    cudaStream_t s) {
-  const int t = 256;
   k_labels<<<grid3d(g), kBlock3d, 0, s>>>(g, L0, u, dst);
 }
 
 // --------------------------------------------------------------------------------------------
 // Multiscale: block mean with edge replication; trilinear cell-centred upsampling.
+template <typename DT>
 __global__ void k_downsample(Grid f, Grid c, int factor, const float* __restrict__ src,
-                             float* __restrict__ dst) {
+                             DT* __restrict__ dst) {
   int x, y, z, idx;
   if (!voxel3d(c, x, y, z, idx)) return;
   double s = 0.0;
@@ -348,29 +377,59 @@ __global__ void k_downsample(Grid f, Grid c, int factor, const float* __restrict
       }
     }
   }
-  dst[idx] = (float)(s / (double)(factor * factor * factor));
+  stf(dst + idx, (float)(s / (double)(factor * factor * factor)));
 }
 
 void launch_downsample(const Grid& fine, const Grid& coarse, int factor, const float* src,
-                       float* dst, cudaStream_t s) {
-  const int t = 256;
-  k_downsample<<<grid3d(coarse), kBlock3d, 0, s>>>(fine, coarse, factor, src, dst);
+                       void* dst, cudaStream_t s, int st) {
+  if (st) k_downsample<<<grid3d(coarse), kBlock3d, 0, s>>>(fine, coarse, factor, src, (__nv_bfloat16*)dst);
+  else k_downsample<<<grid3d(coarse), kBlock3d, 0, s>>>(fine, coarse, factor, src, (float*)dst);
 }
 
-__global__ void k_upsample(Grid c, Grid f, float ratio, const float* __restrict__ src,
-                           float* __restrict__ dst, int nfields) {
+template <typename ST>
+__global__ void k_upsample(Grid c, Grid f, float ratio, const ST* __restrict__ src,
+                           ST* __restrict__ dst, int nfields) {
   int x, y, z, idx;
   if (!voxel3d(f, x, y, z, idx)) return;
   Tri w = tri_setup(c, ((float)x + 0.5f) * ratio - 0.5f, ((float)y + 0.5f) * ratio - 0.5f,
                     ((float)z + 0.5f) * ratio - 0.5f);
   for (int k = 0; k < nfields; ++k)
-    dst[(int64_t)k * f.N + idx] = tri_apply(src + (int64_t)k * c.N, w);
+    stf(dst + (int64_t)k * f.N + idx, tri_apply_t(src + (int64_t)k * c.N, w));
 }
 
-void launch_upsample(const Grid& coarse, const Grid& fine, float ratio, const float* src,
-                     float* dst, int nfields, cudaStream_t s) {
-  const int t = 256;
-  k_upsample<<<grid3d(fine), kBlock3d, 0, s>>>(coarse, fine, ratio, src, dst, nfields);
+void launch_upsample(const Grid& coarse, const Grid& fine, float ratio, const void* src,
+                     void* dst, int nfields, cudaStream_t s, int st) {
+  if (st)
+    k_upsample<<<grid3d(fine), kBlock3d, 0, s>>>(coarse, fine, ratio, (const __nv_bfloat16*)src,
+                                                 (__nv_bfloat16*)dst, nfields);
+  else
+    k_upsample<<<grid3d(fine), kBlock3d, 0, s>>>(coarse, fine, ratio, (const float*)src,
+                                                 (float*)dst, nfields);
+}
+
+// --------------------------------------------------------------------------------------------
+// Storage conversion (fp32 <-> bf16, round to nearest) for the precision form.
+__global__ void k_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) b[i] = __float2bfloat16_rn(a[i]);
+}
+__global__ void k_to_f32(const __nv_bfloat16* __restrict__ a, float* __restrict__ b, int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) b[i] = __bfloat162float(a[i]);
+}
+
+void launch_to_storage(const float* src, void* dst, int64_t n, cudaStream_t s, int st) {
+  if (n <= 0) return;
+  if (st) k_to_bf16<<<152 * 8, 256, 0, s>>>(src, (__nv_bfloat16*)dst, n);
+  else cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
+}
+
+void launch_from_storage(const void* src, float* dst, int64_t n, cudaStream_t s, int st) {
+  if (n <= 0) return;
+  if (st) k_to_f32<<<152 * 8, 256, 0, s>>>((const __nv_bfloat16*)src, dst, n);
+  else cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToDevice, s);
 }
 
 // --------------------------------------------------------------------------------------------

@@ -61,6 +61,8 @@ struct lddmm_ctx {
   int iter = 0;
   double last_E = -1.0;
   float eps = 0.f;
+  int st = 0;               // storage of v and images: 0 float, 1 bf16
+  size_t es = 4;            // bytes per stored element
   std::string err;
   // timing of every kernel launch (lddmm_profile_start / lddmm_profile_stop)
   bool prof_on = false;
@@ -171,6 +173,7 @@ int validate(const lddmm_params* p, std::string& why) {
     why = "tensor-core K needs every axis <= 512 (TMEM columns)"; return LDDMM_ERR_INVALID_ARG;
   }
   if (p->flags & ~3) { why = "unknown flag bits"; return LDDMM_ERR_INVALID_ARG; }
+  if (p->storage != 0 && p->storage != 1) { why = "storage must be 0 (float) or 1 (bf16)"; return LDDMM_ERR_INVALID_ARG; }
   return LDDMM_OK;
 }
 
@@ -205,20 +208,27 @@ int check_finite(lddmm_ctx* ctx, const float* d, int64_t n, const char* what) {
 int load_images(lddmm_ctx* ctx, const float* I0, const float* I1, const float* M) {
   Level& F = ctx->levels.back();
   const int64_t N = F.g.N;
-  CK(cudaMemcpyAsync(F.I0, I0, N * sizeof(float), cudaMemcpyDefault, ctx->stream));
-  CK(cudaMemcpyAsync(F.I1, I1, N * sizeof(float), cudaMemcpyDefault, ctx->stream));
-  if (M) CK(cudaMemcpyAsync(F.M, M, N * sizeof(float), cudaMemcpyDefault, ctx->stream));
-  else launch_fill(F.M, N, 1.0f, ctx->stream);
+  // inputs are float32: stage them (I0 | I1 | M), check them, store them in the storage type
+  float* s0 = ctx->stage;
+  float* s1 = ctx->stage + N;
+  float* s2 = ctx->stage + 2 * N;
+  CK(cudaMemcpyAsync(s0, I0, N * sizeof(float), cudaMemcpyDefault, ctx->stream));
+  CK(cudaMemcpyAsync(s1, I1, N * sizeof(float), cudaMemcpyDefault, ctx->stream));
+  if (M) CK(cudaMemcpyAsync(s2, M, N * sizeof(float), cudaMemcpyDefault, ctx->stream));
+  else launch_fill(s2, N, 1.0f, ctx->stream);
   CK(cudaGetLastError());
   int rc;
-  if ((rc = check_finite(ctx, F.I0, N, "I0"))) return rc;
-  if ((rc = check_finite(ctx, F.I1, N, "I1"))) return rc;
-  if ((rc = check_finite(ctx, F.M, N, "M"))) return rc;
+  if ((rc = check_finite(ctx, s0, N, "I0"))) return rc;
+  if ((rc = check_finite(ctx, s1, N, "I1"))) return rc;
+  if ((rc = check_finite(ctx, s2, N, "M"))) return rc;
+  launch_to_storage(s0, F.I0, N, ctx->stream, ctx->st);
+  launch_to_storage(s1, F.I1, N, ctx->stream, ctx->st);
+  launch_to_storage(s2, F.M, N, ctx->stream, ctx->st);
   for (size_t l = 0; l + 1 < ctx->levels.size(); ++l) {
     Level& L = ctx->levels[l];
-    launch_downsample(F.g, L.g, L.factor, F.I0, L.I0, ctx->stream);
-    launch_downsample(F.g, L.g, L.factor, F.I1, L.I1, ctx->stream);
-    launch_downsample(F.g, L.g, L.factor, F.M, L.M, ctx->stream);
+    launch_downsample(F.g, L.g, L.factor, s0, L.I0, ctx->stream, ctx->st);
+    launch_downsample(F.g, L.g, L.factor, s1, L.I1, ctx->stream, ctx->st);
+    launch_downsample(F.g, L.g, L.factor, s2, L.M, ctx->stream, ctx->st);
   }
   CK(cudaGetLastError());
   ctx->maps_valid = false;
@@ -243,6 +253,11 @@ void release(lddmm_ctx* ctx) {
 }
 
 inline float dtv(const lddmm_ctx* ctx, float h) { return 1.0f / (float)ctx->p.T / h; }
+
+// v_j in the storage type (3 components of N elements each)
+inline void* vptr(const lddmm_ctx* ctx, int j, int64_t N) {
+  return reinterpret_cast<char*>(ctx->v) + (size_t)j * 3 * N * ctx->es;
+}
 
 int reset_acc(lddmm_ctx* ctx) {
   Acc a{};
@@ -297,8 +312,8 @@ int run_step(lddmm_ctx* ctx) {
   int pb = 0;
   for (int j = T - 1; j >= 0; --j) {
     float* uc = ctx->uB[pb];
-    launch_flow_back(g, ctx->v + (int64_t)j * 3 * N, un, uc, L.I1, L.M, ctx->J1 + j * N,
-                     ctx->W + j * N, dtx, dty, dtz, ctx->acc, s, hk);
+    launch_flow_back(g, vptr(ctx, j, N), un, uc, L.I1, L.M, ctx->J1 + j * N, ctx->W + j * N, dtx,
+                     dty, dtz, ctx->acc, s, hk, ctx->st);
     un = uc;
     pb ^= 1;
   }
@@ -308,19 +323,27 @@ int run_step(lddmm_ctx* ctx) {
   const float* uc = nullptr;
   int pf = 0;
   for (int j = 0; j < T; ++j) {
-    float* vj = ctx->v + (int64_t)j * 3 * N;
+    void* vj = vptr(ctx, j, N);
     hk(KID_FWD_TERMS, 0);
     launch_fwd_terms(g, uc, L.I0, ctx->J1 + j * N, ctx->W + j * N, ctx->b, c, 1.0f / L.hx,
-                     1.0f / L.hy, 1.0f / L.hz, s);
+                     1.0f / L.hy, 1.0f / L.hz, s, ctx->st);
     hk(KID_FWD_TERMS, 1);
     float* unx = ctx->uF[pf];
     hk(KID_FWD_FLOW, 0);
     launch_fwd_flow(g, vj, uc, unx, dtx, dty, dtz, ctx->p.alpha, ctx->p.gamma,
                     1.0f / (L.hx * L.hx), 1.0f / (L.hy * L.hy), 1.0f / (L.hz * L.hz), j == T - 1,
-                    L.I0, L.I1, L.M, ctx->J0T, ctx->acc, s);
+                    L.I0, L.I1, L.M, ctx->J0T, ctx->acc, s, ctx->st);
     hk(KID_FWD_FLOW, 1);
-    // K b_j and the update v_j <- v_j - eps (2 v_j - K b_j)
-    CK(apply_K(L.kp, ctx->p.k_mode, ctx->b, ctx->b, ctx->work, 3, s, hk, vj, ctx->eps));
+    // K b_j and the update v_j <- v_j - eps (2 v_j - K b_j): fused into the last DFT pass for
+    // float storage, a separate pass for bf16 storage
+    if (ctx->st == 0) {
+      CK(apply_K(L.kp, ctx->p.k_mode, ctx->b, ctx->b, ctx->work, 3, s, hk, (float*)vj, ctx->eps));
+    } else {
+      CK(apply_K(L.kp, ctx->p.k_mode, ctx->b, ctx->b, ctx->work, 3, s, hk));
+      hk(KID_UPDATE, 0);
+      launch_update(g, vj, ctx->b, ctx->eps, s, ctx->st);
+      hk(KID_UPDATE, 1);
+    }
     uc = unx;
     pf ^= 1;
   }
@@ -346,7 +369,7 @@ int refresh_maps(lddmm_ctx* ctx, bool energy) {
   int pb = 0;
   for (int j = T - 1; j >= 0; --j) {
     float* uc = ctx->uB[pb];
-    launch_flow_only_back(g, ctx->v + (int64_t)j * 3 * N, un, uc, dtx, dty, dtz, s);
+    launch_flow_only_back(g, vptr(ctx, j, N), un, uc, dtx, dty, dtz, s, ctx->st);
     un = uc;
     pb ^= 1;
   }
@@ -355,9 +378,10 @@ int refresh_maps(lddmm_ctx* ctx, bool energy) {
   int pf = 0;
   for (int j = 0; j < T; ++j) {
     float* unx = ctx->uF[pf];
-    launch_fwd_flow(g, ctx->v + (int64_t)j * 3 * N, uc, unx, dtx, dty, dtz, ctx->p.alpha,
+    launch_fwd_flow(g, vptr(ctx, j, N), uc, unx, dtx, dty, dtz, ctx->p.alpha,
                     ctx->p.gamma, 1.0f / (L.hx * L.hx), 1.0f / (L.hy * L.hy),
-                    1.0f / (L.hz * L.hz), j == T - 1, L.I0, L.I1, L.M, ctx->J0T, ctx->acc, s);
+                    1.0f / (L.hz * L.hz), j == T - 1, L.I0, L.I1, L.M, ctx->J0T, ctx->acc, s,
+                    ctx->st);
     uc = unx;
     pf ^= 1;
   }
@@ -381,7 +405,7 @@ int change_level(lddmm_ctx* ctx, int level) {
   const Level& B = ctx->levels[level];
   const int T = ctx->p.T;
   launch_upsample(A.g, B.g, (float)B.factor / (float)A.factor, ctx->v, ctx->v_tmp, 3 * T,
-                  ctx->stream);
+                  ctx->stream, ctx->st);
   CK(cudaGetLastError());
   std::swap(ctx->v, ctx->v_tmp);
   ctx->cur = level;
@@ -397,7 +421,7 @@ int do_step(lddmm_ctx* ctx, lddmm_energy* out) {
   // to v_{k-1} (kept in v_prev), halve the step and redo that iteration.
   const bool backtrack = (ctx->p.flags & 1) != 0;
   const Level& L = ctx->levels[ctx->cur];
-  const size_t vbytes = (size_t)ctx->p.T * 3 * L.g.N * sizeof(float);
+  const size_t vbytes = (size_t)ctx->p.T * 3 * L.g.N * ctx->es;
   for (int attempt = 0; attempt < 30; ++attempt) {
     if (backtrack) CK(cudaMemcpyAsync(ctx->v_tmp, ctx->v, vbytes, cudaMemcpyDeviceToDevice, ctx->stream));
     int rc = run_step(ctx);
@@ -455,6 +479,8 @@ int lddmm_create(const lddmm_params* p, const float* I0, const float* I1, const 
   if (!ctx) return fail(nullptr, LDDMM_ERR_OOM, "host allocation failed");
   ctx->p = *p;
   ctx->eps = p->epsilon;
+  ctx->st = p->storage;
+  ctx->es = p->storage ? 2 : 4;
   auto bail = [&](int code) {
     std::string msg = ctx->err;
     release(ctx);
@@ -494,19 +520,21 @@ int lddmm_create(const lddmm_params* p, const float* I0, const float* I1, const 
   bool ok = true;
   for (int l = 0; l < nl && ok; ++l) {
     Level& L = ctx->levels[l];
-    ok = A(dalloc(&L.I0, L.g.N)) && A(dalloc(&L.I1, L.g.N)) && A(dalloc(&L.M, L.g.N)) &&
+    const int64_t ie = (L.g.N * (int64_t)ctx->es + 3) / 4;   // image storage, in floats
+    ok = A(dalloc(&L.I0, ie)) && A(dalloc(&L.I1, ie)) && A(dalloc(&L.M, ie)) &&
          A(kplan_create(&L.kp, L.g.nx, L.g.ny, L.g.nz, L.hx, L.hy, L.hz, p->alpha, p->gamma));
   }
-  ok = ok && A(dalloc(&ctx->v, T * 3 * N)) && A(dalloc(&ctx->v_tmp, T * 3 * N)) &&
+  const int64_t ve = (T * 3 * N * (int64_t)ctx->es + 3) / 4;  // velocity storage, in floats
+  ok = ok && A(dalloc(&ctx->v, ve)) && A(dalloc(&ctx->v_tmp, ve)) &&
        A(dalloc(&ctx->uB[0], 3 * N)) && A(dalloc(&ctx->uB[1], 3 * N)) &&
        A(dalloc(&ctx->uF[0], 3 * N)) && A(dalloc(&ctx->uF[1], 3 * N)) &&
        A(dalloc(&ctx->J1, T * N)) && A(dalloc(&ctx->W, T * N)) && A(dalloc(&ctx->b, 3 * N)) &&
        A(dalloc(&ctx->work, 3 * N)) && A(dalloc(&ctx->J0T, N)) && A(dalloc(&ctx->stage, 3 * N)) &&
        A(dalloc(&ctx->acc, 1)) && A(dalloc(&ctx->flag, 1)) && A(dalloc(&ctx->hist, 3 * 65536)) &&
        A(cudaMallocHost((void**)&ctx->acc_host, sizeof(Acc)));
-  if (ok && (p->flags & 1)) ok = A(dalloc(&ctx->v_prev, T * 3 * N));
+  if (ok && (p->flags & 1)) ok = A(dalloc(&ctx->v_prev, ve));
   if (!ok) return bail(LDDMM_ERR_OOM);
-  if (cudaMemsetAsync(ctx->v, 0, (size_t)T * 3 * N * sizeof(float), ctx->stream) != cudaSuccess) {
+  if (cudaMemsetAsync(ctx->v, 0, (size_t)ve * sizeof(float), ctx->stream) != cudaSuccess) {
     ctx->err = "memset failed";
     return bail(LDDMM_ERR_CUDA);
   }
@@ -599,16 +627,32 @@ int lddmm_transfer_labels(lddmm_ctx* ctx, const uint16_t* L0, uint16_t* dst) {
 int lddmm_get_velocity(lddmm_ctx* ctx, float* dst) {
   if (!ctx || !dst) return fail(ctx, LDDMM_ERR_INVALID_ARG, "NULL argument");
   const Grid& g = ctx->levels[ctx->cur].g;
-  return copy_out(ctx, dst, ctx->v, (size_t)ctx->p.T * 3 * g.N * sizeof(float));
+  if (ctx->st == 0) return copy_out(ctx, dst, ctx->v, (size_t)ctx->p.T * 3 * g.N * sizeof(float));
+  // bf16 storage: convert one time step at a time through the staging buffer
+  for (int j = 0; j < ctx->p.T; ++j) {
+    launch_from_storage(vptr(ctx, j, g.N), ctx->stage, 3 * (int64_t)g.N, ctx->stream, ctx->st);
+    int rc = copy_out(ctx, dst + (size_t)j * 3 * g.N, ctx->stage, (size_t)3 * g.N * sizeof(float));
+    if (rc) return rc;
+  }
+  return wait_stream(ctx);
 }
 
 int lddmm_set_velocity(lddmm_ctx* ctx, const float* src) {
   if (!ctx || !src) return fail(ctx, LDDMM_ERR_INVALID_ARG, "NULL argument");
   const Grid& g = ctx->levels[ctx->cur].g;
   const int64_t n = (int64_t)ctx->p.T * 3 * g.N;
-  CK(cudaMemcpyAsync(ctx->v, src, n * sizeof(float), cudaMemcpyDefault, ctx->stream));
-  int rc = check_finite(ctx, ctx->v, n, "velocity");
-  if (rc) return rc;
+  int rc;
+  if (ctx->st == 0) {
+    CK(cudaMemcpyAsync(ctx->v, src, n * sizeof(float), cudaMemcpyDefault, ctx->stream));
+    if ((rc = check_finite(ctx, ctx->v, n, "velocity"))) return rc;
+  } else {
+    for (int j = 0; j < ctx->p.T; ++j) {
+      CK(cudaMemcpyAsync(ctx->stage, src + (size_t)j * 3 * g.N, (size_t)3 * g.N * sizeof(float),
+                         cudaMemcpyDefault, ctx->stream));
+      if ((rc = check_finite(ctx, ctx->stage, 3 * (int64_t)g.N, "velocity"))) return rc;
+      launch_to_storage(ctx->stage, vptr(ctx, j, g.N), 3 * (int64_t)g.N, ctx->stream, ctx->st);
+    }
+  }
   ctx->maps_valid = false;
   ctx->j0_valid = false;
   ctx->last_E = -1.0;
@@ -628,9 +672,14 @@ int lddmm_get_field(lddmm_ctx* ctx, int which, float* dst) {
       if (which == LDDMM_FIELD_U10) return copy_out(ctx, dst, ctx->u10, 3 * N * sizeof(float));
       if (which == LDDMM_FIELD_U01) return copy_out(ctx, dst, ctx->u01, 3 * N * sizeof(float));
       return copy_out(ctx, dst, ctx->J0T, N * sizeof(float));
-    case LDDMM_FIELD_I0: return copy_out(ctx, dst, L.I0, N * sizeof(float));
-    case LDDMM_FIELD_I1: return copy_out(ctx, dst, L.I1, N * sizeof(float));
-    case LDDMM_FIELD_M: return copy_out(ctx, dst, L.M, N * sizeof(float));
+    case LDDMM_FIELD_I0:
+    case LDDMM_FIELD_I1:
+    case LDDMM_FIELD_M: {
+      const void* src = which == LDDMM_FIELD_I0 ? (const void*)L.I0
+                        : which == LDDMM_FIELD_I1 ? (const void*)L.I1 : (const void*)L.M;
+      launch_from_storage(src, ctx->stage, N, ctx->stream, ctx->st);
+      return copy_out(ctx, dst, ctx->stage, N * sizeof(float));
+    }
     default: return fail(ctx, LDDMM_ERR_INVALID_ARG, "unknown field");
   }
 }
@@ -728,6 +777,7 @@ int lddmm_profile_stop(lddmm_ctx* ctx, lddmm_kernel_stat* out, int max_out, int*
 
 int lddmm_energy_grad(lddmm_ctx* ctx, const float* v, float* grad, double* E) {
   if (!ctx || !grad) return fail(ctx, LDDMM_ERR_INVALID_ARG, "NULL argument");
+  if (ctx->st != 0) return fail(ctx, LDDMM_ERR_INVALID_ARG, "the exact gradient needs float storage");
   const Level& L = ctx->levels[ctx->cur];
   const Grid& g = L.g;
   const int T = ctx->p.T;
@@ -773,7 +823,7 @@ int lddmm_energy_grad(lddmm_ctx* ctx, const float* v, float* grad, double* E) {
     float* unx = keep ? slot_of(j + 1) : ctx->uF[pf];
     launch_fwd_flow(g, ctx->v + (int64_t)j * F, uc, unx, dtx, dty, dtz, ctx->p.alpha,
                     ctx->p.gamma, ihx2, ihy2, ihz2, j == T - 1, L.I0, L.I1, L.M, ctx->J0T,
-                    ctx->acc, s);
+                    ctx->acc, s, 0);
     uc = unx;
     if (!keep) pf ^= 1;
   }
@@ -797,7 +847,7 @@ int lddmm_energy_grad(lddmm_ctx* ctx, const float* v, float* grad, double* E) {
         CK(cudaMemcpyAsync(ctx->seg, slot_of(k), F * sizeof(float), cudaMemcpyDeviceToDevice, s));
         for (int i = 1; i < c && k + i < T; ++i)
           launch_flow_only_fwd(g, ctx->v + (int64_t)(k + i - 1) * F, ctx->seg + (size_t)(i - 1) * F,
-                               ctx->seg + (size_t)i * F, dtx, dty, dtz, s);
+                               ctx->seg + (size_t)i * F, dtx, dty, dtz, s, 0);
         seg_base = k;
       }
       uj = ctx->seg + (size_t)(j - k) * F;

@@ -44,7 +44,8 @@ class lddmm_params(ctypes.Structure):
                 ("alpha", ctypes.c_float), ("gamma", ctypes.c_float), ("sigma", ctypes.c_float),
                 ("epsilon", ctypes.c_float), ("iterations", ctypes.c_int),
                 ("num_levels", ctypes.c_int), ("level_factor", ctypes.c_int * 4),
-                ("k_mode", ctypes.c_int), ("flags", ctypes.c_int), ("timeout_s", ctypes.c_float)]
+                ("k_mode", ctypes.c_int), ("flags", ctypes.c_int), ("timeout_s", ctypes.c_float),
+                ("storage", ctypes.c_int)]
 
 
 class lddmm_energy(ctypes.Structure):
