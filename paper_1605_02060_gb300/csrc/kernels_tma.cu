@@ -34,9 +34,8 @@ constexpr int W_CONV = 4, W_PA = 12, W_PB = 13, W_MMA = 14;
 constexpr int NCONV = 256;
 constexpr int RAWB = 128 * 16 * 4;   // fp32 A slice
 constexpr int OPB = 128 * 16 * 2;    // one bf16 operand slice (hi or lo)
-constexpr int NB = 4;               // staging buffers per epilogue warp
+constexpr int NBMAX = 4;            // staging buffers per epilogue warp (at most)
 constexpr int WSTGB = 32 * 16 * 4;  // one staging buffer: 32 lines x 16 columns fp32
-constexpr int STGB = 4 * NB * WSTGB; // all epilogue staging
 
 struct TmaArgs {
   const float* vupd;   // update epilogue: v (read), written through the store map
@@ -54,12 +53,18 @@ struct TmaArgs {
   int split;
   int dbuf;
   int RS, PS;          // raw-ring and operand-ring depths
+  int bres;            // 1: the whole B table is loaded once and stays in shared memory
+  int nb;              // staging buffers per epilogue warp (4 for the update, else 2)
   int* err;
 };
 
-__host__ __device__ inline int op_slot_bytes(int Npad) { return 2 * OPB + Npad * 64; }
-__host__ __device__ inline int smem_bytes(int Npad, int RS, int PS) {
-  return RS * RAWB + PS * op_slot_bytes(Npad) + STGB;
+// operand slot: A hi and lo, plus the k-step's B slice unless B is resident
+__host__ __device__ inline int op_slot_bytes(int Npad, int bres) {
+  return 2 * OPB + (bres ? 0 : Npad * 64);
+}
+__host__ __device__ inline int stage_bytes(int nb) { return 4 * nb * WSTGB; }
+__host__ __device__ inline int smem_bytes(int Npad, int RS, int PS, int bres, int nb) {
+  return RS * RAWB + PS * op_slot_bytes(Npad, bres) + (bres ? Npad * Npad * 4 : 0) + stage_bytes(nb);
 }
 
 __device__ __forceinline__ uint32_t kmaj(int row, int kk) {
@@ -114,7 +119,7 @@ __global__ void __launch_bounds__(NT, 1) k_dft_tma(const __grid_constant__ CUten
                                                    TmaArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(8) uint64_t b_rfull[16], b_rempty[16], b_pB[8], b_pconv[8], b_pempty[8];
-  __shared__ __align__(8) uint64_t b_tfull[2], b_tempty[2], b_fin, b_v[4 * NB];
+  __shared__ __align__(8) uint64_t b_tfull[2], b_tempty[2], b_fin, b_v[4 * NBMAX], b_bres;
   __shared__ uint32_t tmem_sh;
   __shared__ int abort_sh;
 
@@ -122,8 +127,9 @@ __global__ void __launch_bounds__(NT, 1) k_dft_tma(const __grid_constant__ CUten
   const int RS = a.RS, PS = a.PS;
   uint8_t* raw_ring = smem;
   uint8_t* op_ring = smem + RS * RAWB;
-  uint8_t* stage = op_ring + PS * op_slot_bytes(a.Npad);
-  const int osb = op_slot_bytes(a.Npad);
+  const int osb = op_slot_bytes(a.Npad, a.bres);
+  uint8_t* barea = op_ring + PS * osb;                      // resident B (bres)
+  uint8_t* stage = barea + (a.bres ? a.Npad * a.Npad * 4 : 0);
   volatile int* abort = &abort_sh;
 
   if (warp == W_MMA) {
@@ -145,7 +151,8 @@ __global__ void __launch_bounds__(NT, 1) k_dft_tma(const __grid_constant__ CUten
       ptx::mbar_init(ptx::smem_u32(&b_tempty[i]), 128);
     }
     ptx::mbar_init(ptx::smem_u32(&b_fin), 1);
-    for (int i = 0; i < 4 * NB; ++i) ptx::mbar_init(ptx::smem_u32(&b_v[i]), 1);
+    ptx::mbar_init(ptx::smem_u32(&b_bres), 1);
+    for (int i = 0; i < 4 * NBMAX; ++i) ptx::mbar_init(ptx::smem_u32(&b_v[i]), 1);
     ptx::fence_mbar_init();
     abort_sh = 0;
   }
@@ -182,7 +189,15 @@ __global__ void __launch_bounds__(NT, 1) k_dft_tma(const __grid_constant__ CUten
     }
   } else if (warp == W_PB) {
     // ------------------------------------------------------------ B producer (bulk copies)
-    if (lane == 0) {
+    if (lane == 0 && a.bres) {
+      // resident B: every k-step slice once, in the same per-step layout
+      const uint32_t fb = ptx::smem_u32(&b_bres);
+      ptx::mbar_arrive_expect_tx(fb, (uint32_t)(nk * a.Npad * 64));
+      for (int s = 0; s < nk; ++s)
+        ptx::bulk_load(ptx::smem_u32(barea + (size_t)s * a.Npad * 64), a.B + (size_t)s * a.Npad * 4,
+                       (uint32_t)a.Npad * 64u, fb);
+      ptx::mbar_wait(fb, 0u);
+    } else if (lane == 0) {
       uint32_t g = 0;
       for (; g < total; ++g) {
         const int s = (int)(g % nk), p = (int)(g % PS);
@@ -231,6 +246,7 @@ __global__ void __launch_bounds__(NT, 1) k_dft_tma(const __grid_constant__ CUten
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       uint32_t g = 0;
+      if (a.bres && !ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bres), 0u, abort)) goto mma_done;
       for (int i = 0; i < my_tiles; ++i) {
         const int ab = a.dbuf ? (i & 1) : 0;
         const uint32_t use = a.dbuf ? (uint32_t)(i >> 1) : (uint32_t)i;
@@ -242,11 +258,15 @@ __global__ void __launch_bounds__(NT, 1) k_dft_tma(const __grid_constant__ CUten
           const int p = (int)(g % PS);
           const uint32_t par = (g / PS) & 1;
           if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_pconv[p]), par, abort) ||
-              !ptx::mbar_wait_or_abort(ptx::smem_u32(&b_pB[p]), par, abort)) { ok = false; break; }
+              (!a.bres && !ptx::mbar_wait_or_abort(ptx::smem_u32(&b_pB[p]), par, abort))) {
+            ok = false;
+            break;
+          }
           ptx::tc_fence_after();
           const uint32_t op = ptx::smem_u32(op_ring + p * osb);
           const uint32_t a_hi = op, a_lo = op + OPB;
-          const uint32_t b_hi = op + 2 * OPB, b_lo = b_hi + (uint32_t)a.Npad * 32u;
+          const uint32_t b_hi = a.bres ? ptx::smem_u32(barea + (size_t)s * a.Npad * 64) : op + 2 * OPB;
+          const uint32_t b_lo = b_hi + (uint32_t)a.Npad * 32u;
           for (int n0 = 0; n0 < a.Npad; n0 += 256) {
             const int nc = min(256, a.Npad - n0);
             const uint32_t id = ptx::idesc_bf16(128, nc);
@@ -266,6 +286,7 @@ __global__ void __launch_bounds__(NT, 1) k_dft_tma(const __grid_constant__ CUten
         if (!ok) break;
         ptx::mma_commit(ptx::smem_u32(&b_tfull[ab]));
       }
+    mma_done:
       ptx::mma_commit(ptx::smem_u32(&b_fin));
     }
   } else {
@@ -274,8 +295,9 @@ __global__ void __launch_bounds__(NT, 1) k_dft_tma(const __grid_constant__ CUten
     // buffers (32 lines x 16 columns); lane 0 issues that warp's TMA stores (and, for the update,
     // the TMA loads of v that are prefetched NB-1 chunks ahead).
     const int q = warp;
+    const int NB = a.nb;
     uint8_t* wst = stage + q * (NB * WSTGB);
-    const uint32_t vbar0 = ptx::smem_u32(&b_v[q * NB]);
+    const uint32_t vbar0 = ptx::smem_u32(&b_v[q * NBMAX]);
     if (lane == 0) ptx::prefetch_tmap(&tmO);
     const int nch = a.Npad / 16;
     uint32_t cc = 0;      // chunks processed by this warp (ring position)
@@ -487,18 +509,21 @@ cudaError_t tma_axis_pass(const KPlan& kp, int axis, bool inverse, int split, co
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-  // ring depths within ~220 KB of shared memory: operand ring 4 deep, the rest raw slots
-  a.PS = 4;
-  const int budget = 220 * 1024;
-  int RS = (budget - a.PS * op_slot_bytes(a.Npad) - STGB) / RAWB;
-  if (RS > 16) RS = 16;
-  if (RS < 2) {
-    a.PS = 2;
-    RS = (budget - a.PS * op_slot_bytes(a.Npad) - STGB) / RAWB;
-  }
-  if (RS < 2) return cudaErrorNotSupported;
-  a.RS = RS;
-  const int smem = smem_bytes(a.Npad, a.RS, a.PS);
+  // Shared memory (<= 225 KB): 6 raw slots for the TMA loads (measured: deeper raw rings at
+  // the expense of operand slots are slower), 4 staging buffers per epilogue warp, B resident
+  // when its whole table fits (the y pass) or streamed with the operand slots, and the rest of
+  // the budget for operand slots (at most 8).
+  const int budget = 225 * 1024;
+  a.nb = 4;
+  const int stg = stage_bytes(a.nb);
+  const int bbytes = a.Npad * a.Npad * 4;
+  a.RS = 6;
+  a.bres = (a.RS * RAWB + bbytes + 3 * 2 * OPB + stg <= budget) ? 1 : 0;
+  int PS = (budget - a.RS * RAWB - (a.bres ? bbytes : 0) - stg) / op_slot_bytes(a.Npad, a.bres);
+  if (PS > 8) PS = 8;
+  if (PS < 2) return cudaErrorNotSupported;
+  a.PS = PS;
+  const int smem = smem_bytes(a.Npad, a.RS, a.PS, a.bres, a.nb);
   cudaError_t e = cudaFuncSetAttribute(k_dft_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   if (!g_num_sms) {
