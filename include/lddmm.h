@@ -187,6 +187,40 @@ int lddmm_profile_stop(lddmm_ctx* ctx, lddmm_kernel_stat* out, int max_out, int*
 int lddmm_apply_K_noalloc(const float* src, float* dst, int nx, int ny, int nz, float hx,
                           float hy, float hz, float alpha, float gamma, void* stream);
 
+/* ---- Learned warm start: kernels of a 3D convolutional encoder-decoder that predicts an initial
+ * velocity from a mask pair (no counterpart in the paper: §2.4 optimises from v = 0).  All pointers are device
+ * pointers; work is enqueued on `stream` (NULL = legacy default stream); LDDMM_ERR_INVALID_ARG
+ * on a bad shape, LDDMM_ERR_CUDA on a launch failure.  Layout: activations [B][C][n][n][n]
+ * float32; weights [Co][Ci][k^3] bf16 (k = 3, zero padding 1, or k = 1); FP32 accumulation. */
+/* y (+)= conv(x, w) + bias (bias may be NULL), then ReLU if relu. */
+int lddmm_net_conv3d_fwd(const float* x, const void* w_bf16, const float* bias, float* y, int B,
+                         int Ci, int Co, int n, int ksize, int relu, int accumulate, void* stream);
+/* dx = data gradient of the convolution for output gradient dy; wT_scratch holds Ci*Co*k^3
+ * bf16 (the transposed, flipped kernel). */
+int lddmm_net_conv3d_dgrad(const float* dy, const void* w_bf16, void* wT_scratch, float* dx, int B,
+                           int Ci, int Co, int n, int ksize, void* stream);
+/* dw += weight gradient (float32 [Co][Ci][k^3]), db += bias gradient (NULL: skipped). */
+int lddmm_net_conv3d_wgrad(const float* x, const float* dy, float* dw, float* db, int B, int Ci,
+                           int Co, int n, int ksize, void* stream);
+/* dy[i] = 0 where y[i] <= 0 (ReLU backward on the stored output). */
+int lddmm_net_relu_bwd(float* dy, const float* y, int64_t count, void* stream);
+/* 2x average pooling of BC volumes of n^3 (backward: src = coarse gradient, dst = fine). */
+int lddmm_net_pool2(const float* src, float* dst, int64_t BC, int n, int backward, void* stream);
+/* 2x nearest upsampling of [B][C][m^3] into channels [coff, coff+C) of a [B][Cy][(2m)^3]
+ * buffer (backward: sums the 8 children back). */
+int lddmm_net_up2(const float* src, float* dst, int B, int C, int m, int Cy, int coff, int backward,
+                  void* stream);
+/* dst[b][doff+c] (+)= src[b][soff+c] for c < C, nv voxels per channel (concatenation). */
+int lddmm_net_copy_channels(const float* src, float* dst, int B, int C, int64_t nv, int Cs,
+                            int soff, int Cd, int doff, int accumulate, void* stream);
+/* *loss_dev += sum (pred - target)^2 (FP64); grad = 2 (pred - target) / count (NULL: skipped). */
+int lddmm_net_mse(const float* pred, const float* target, float* grad, int64_t count,
+                  double* loss_dev, void* stream);
+/* Adam step `step` (>= 1) on FP32 master weights w with moments m, v; refreshes the bf16 copy. */
+int lddmm_net_adam(float* w, const float* g, float* m, float* v, void* w_bf16, int64_t count,
+                   float lr, float beta1, float beta2, float eps, int step, void* stream);
+int lddmm_net_cast_bf16(const float* a, void* b, int64_t count, void* stream);
+
 /* Change the bound on host waits for this context (seconds, <= 0: 600 s). */
 int lddmm_set_timeout(lddmm_ctx* ctx, float seconds);
 

@@ -97,6 +97,18 @@ _SIGS = {
     "lddmm_profile_start": (ctypes.c_int, [_P, ctypes.c_int]),
     "lddmm_profile_stop": (ctypes.c_int, [_P, ctypes.POINTER(lddmm_kernel_stat), ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int)]),
+    "lddmm_net_conv3d_fwd": (ctypes.c_int, [_P, _P, _P, _P] + [ctypes.c_int] * 7 + [_P]),
+    "lddmm_net_conv3d_dgrad": (ctypes.c_int, [_P, _P, _P, _P] + [ctypes.c_int] * 5 + [_P]),
+    "lddmm_net_conv3d_wgrad": (ctypes.c_int, [_P, _P, _P, _P] + [ctypes.c_int] * 5 + [_P]),
+    "lddmm_net_relu_bwd": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
+    "lddmm_net_pool2": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P]),
+    "lddmm_net_up2": (ctypes.c_int, [_P, _P] + [ctypes.c_int] * 6 + [_P]),
+    "lddmm_net_copy_channels": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int64]
+                                + [ctypes.c_int] * 5 + [_P]),
+    "lddmm_net_mse": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
+    "lddmm_net_adam": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_float,
+                                      ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int, _P]),
+    "lddmm_net_cast_bf16": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "lddmm_last_error": (ctypes.c_char_p, [_P]),
     "lddmm_destroy": (None, [_P]),
 }

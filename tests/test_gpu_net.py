@@ -1,0 +1,158 @@
+"""GPU checks of the warm-start network kernels against the FP64 oracle (same bf16-rounded
+weights), of whole-network gradients, of Adam, and of the gain of the trained network: a warm
+start from its prediction reaches the plain method's energy in fewer iterations."""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1605_02060_gb300 import build
+    build.build()
+    from paper_1605_02060_gb300 import lddmm as L
+    return L.load()
+
+
+P = lambda t: ctypes.c_void_p(t.data_ptr())
+
+
+def _bf(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16)
+
+
+@pytest.mark.parametrize("B,Ci,Co,n,k", [(2, 5, 18, 8, 3), (1, 3, 4, 12, 3), (2, 16, 3, 8, 1),
+                                        (1, 9, 33, 4, 3)])
+def test_conv_kernels_match_oracle(lib, B, Ci, Co, n, k):
+    from oracle import surrogate as S
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((B, Ci, n, n, n)).astype(np.float32)
+    w = rng.standard_normal((Co, Ci, k ** 3)).astype(np.float32)
+    b = rng.standard_normal(Co).astype(np.float32)
+    dy = rng.standard_normal((B, Co, n, n, n)).astype(np.float32)
+    wb = _bf(w)
+    wq = wb.float().numpy()
+    xd, dyd, bd = (torch.from_numpy(a).cuda() for a in (x, dy, b))
+    wbd = wb.cuda()
+    y = torch.empty((B, Co, n, n, n), device="cuda")
+    assert lib.lddmm_net_conv3d_fwd(P(xd), P(wbd), P(bd), P(y), B, Ci, Co, n, k, 0, 0, None) == 0
+    dx = torch.empty_like(xd)
+    scratch = torch.empty(Ci * Co * k ** 3, dtype=torch.bfloat16, device="cuda")
+    assert lib.lddmm_net_conv3d_dgrad(P(dyd), P(wbd), P(scratch), P(dx), B, Ci, Co, n, k, None) == 0
+    dw = torch.zeros((Co, Ci, k ** 3), device="cuda")
+    db = torch.zeros(Co, device="cuda")
+    assert lib.lddmm_net_conv3d_wgrad(P(xd), P(dyd), P(dw), P(db), B, Ci, Co, n, k, None) == 0
+    torch.cuda.synchronize()
+    assert _rel(y.cpu().numpy(), S.conv3d(x, wq, b)) < 1e-5
+    assert _rel(dx.cpu().numpy(), S.conv3d_dgrad(dy, wq)) < 1e-5
+    gw, gb = S.conv3d_wgrad(x, dy, k)
+    assert _rel(dw.cpu().numpy(), gw) < 1e-5
+    assert _rel(db.cpu().numpy(), gb) < 1e-5
+
+
+def test_resampling_and_loss_kernels(lib):
+    from oracle import surrogate as S
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((2, 3, 8, 8, 8)).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    p = torch.empty((2, 3, 4, 4, 4), device="cuda")
+    assert lib.lddmm_net_pool2(P(xd), P(p), 6, 8, 0, None) == 0
+    pb = torch.empty_like(xd)
+    assert lib.lddmm_net_pool2(P(p), P(pb), 6, 8, 1, None) == 0
+    u = torch.zeros((2, 5, 16, 16, 16), device="cuda")
+    assert lib.lddmm_net_up2(P(xd), P(u), 2, 3, 8, 5, 1, 0, None) == 0
+    ub = torch.empty_like(xd)
+    assert lib.lddmm_net_up2(P(u), P(ub), 2, 3, 8, 5, 1, 1, None) == 0
+    t = torch.from_numpy(rng.standard_normal(x.shape).astype(np.float32)).cuda()
+    g = torch.empty_like(xd)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    assert lib.lddmm_net_mse(P(xd), P(t), P(g), xd.numel(), P(loss), None) == 0
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(p.cpu().numpy(), S.pool2(x), rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(pb.cpu().numpy(), S.pool2_bwd(S.pool2(x)), rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(u[:, 1:4].cpu().numpy(), S.up2(x), rtol=0, atol=0)
+    np.testing.assert_allclose(ub.cpu().numpy(), S.up2_bwd(S.up2(x)), rtol=1e-6)
+    lo, go = S.mse(x, t.cpu().numpy())
+    assert abs(float(loss) / x.size - lo) <= 1e-6 * lo
+    assert _rel(g.cpu().numpy(), go) < 1e-6
+
+
+def test_adam_matches_oracle(lib):
+    from oracle import surrogate as S
+    rng = np.random.default_rng(2)
+    w = rng.standard_normal(1000).astype(np.float32)
+    m = np.zeros(1000)
+    v = np.zeros(1000)
+    wd, md, vd = (torch.from_numpy(a.astype(np.float32)).cuda() for a in (w, m, v))
+    wo = w.astype(np.float64)
+    for step in range(1, 4):
+        g = rng.standard_normal(1000).astype(np.float32)
+        gd = torch.from_numpy(g).cuda()
+        assert lib.lddmm_net_adam(P(wd), P(gd), P(md), P(vd), None, 1000, 1e-2, 0.9, 0.999, 1e-8,
+                                  step, None) == 0
+        wo, m, v = S.adam(wo, g.astype(np.float64), m, v, 1e-2, 0.9, 0.999, 1e-8, step)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(wd.cpu().numpy(), wo, rtol=1e-5, atol=1e-6)
+
+
+def test_network_gradients_match_oracle(lib):
+    from oracle import surrogate as S
+    from paper_1605_02060_gb300.surrogate import UNet3D
+    chans, B, n = (4, 8, 8), 2, 8
+    net = UNet3D(chans=chans, cout=3, n=n, batch=B, seed=3)
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((B, 2, n, n, n)).astype(np.float32)
+    t = rng.standard_normal((B, 3, n, n, n)).astype(np.float32)
+    y = net.forward(torch.from_numpy(x).cuda())
+    net.loss_and_grad(torch.from_numpy(t).cuda())
+    net.backward(net.dy)
+    torch.cuda.synchronize()
+    params = [(wb.float().cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64))
+              for wb, b in zip(net.wb, net.b)]
+    yo, acts = S.net_forward(params, x, chans)
+    assert _rel(y.cpu().numpy(), yo) < 1e-4
+    _, dyo = S.mse(yo, t)
+    grads = S.net_backward(params, acts, dyo, chans)
+    for i, ((gw, gb), dw, db) in enumerate(zip(grads, net.dw, net.db)):
+        assert _rel(dw.cpu().numpy(), gw) < 1e-3, i
+        assert _rel(db.cpu().numpy(), gb) < 1e-3, i
+
+
+def test_trained_network_warm_start_saves_iterations(lib):
+    """Train on 240 pairs at 32^3 (x8 mirror images) labelled by 60 plain iterations.  On 8
+    held-out pairs: the prediction is closer to the plain field than v = 0, and the warm start
+    (prediction smoothed by gamma^2 K, scale judged by the energy, v = 0 among the candidates)
+    reaches the energy of 60 plain iterations in fewer iterations on average."""
+    from paper_1605_02060_gb300 import surrogate as SG
+    n, T, iters = 32, 10, 60
+    train_pairs = SG.make_pairs(240, n, seed0=1000, amp_max=4.0)
+    X, Y = SG.label_pairs(train_pairs, iters, T)
+    X, Y = SG.augment_flips(X, Y, T)
+    scale = float(np.sqrt((Y ** 2).mean()))
+    net = SG.UNet3D(n=n, batch=8, seed=0, out_scale=scale)
+    hist = SG.train(net, X, Y, epochs=6, lr=1e-3)
+    assert hist[-1] < 0.5 * hist[0], hist
+    warm, rels, cs = [], [], []
+    for pr in SG.make_pairs(8, n, seed0=5000, amp_max=4.0):
+        v, E, _, _ = SG.run_plain(pr, iters, T)
+        pred = SG.warm_start_field(net, pr, T)
+        rels.append(_rel(pred, v.cpu().numpy()))
+        itw, c, nev, _ = SG.run_warm(net, pr, E[-1], 2 * iters, T)
+        warm.append(itw)
+        cs.append(c)
+    print("\nheld-out prediction rel-L2 %s; chosen scales %s; warm iterations to the plain energy "
+          "after %d: %s (mean %.1f)" % (np.round(rels, 3), cs, iters, warm, np.mean(warm)))
+    assert np.mean(rels) < 0.9
+    assert np.mean(warm) < 0.8 * iters, warm
