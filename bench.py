@@ -55,12 +55,14 @@ def _csrc_hash():
 
 # Algorithmic bytes (or flops) per voxel for one launch of each kernel (fp32 storage);
 # the derivation is in the design notes: each field is read or written once per launch.
-def algorithmic(kernel, N, dims, kmode):
+def algorithmic(kernel, N, dims, kmode, T=10):
     X, Y, Z = dims
     B = {"flow_back_disp": 36, "flow_back_terms": 28, "fwd_residual": 36,
-         "fwd_flow_ereg": 36, "update": 36}
+         "fwd_flow": 36, "update": 36}
     if kernel in B:
         return {"bound": "hbm", "bytes": B[kernel] * N}
+    if kernel == "ereg":             # all T velocity fields read once: 12 B per voxel and step
+        return {"bound": "hbm", "bytes": 12 * T * N}
     L = {"K_x_fwd": X, "K_x_inv_update": X, "K_y_fwd": Y, "K_y_inv": Y, "K_z_symbol": Z,
          "K_z_inv": Z}[kernel]
     flops = 2.0 * L * 3 * N          # dense real DFT along one axis, 3 components
@@ -269,7 +271,7 @@ def run_ours(args):
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     name, (nl, tot_ms) = dom
     avg_s = tot_ms / nl / 1000.0
-    alg = algorithmic(name, N, (X, Y, Z), args.kmode)
+    alg = algorithmic(name, N, (X, Y, Z), args.kmode, T)
     traffic = _traffic(name)
     if alg["bound"] == "hbm":
         achieved = alg["bytes"] / avg_s / 1e9

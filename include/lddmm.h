@@ -97,7 +97,7 @@ typedef struct {
 } lddmm_energy;
 
 /* Fill p with the defaults used by the tests: h = 1, T = 10, alpha = 0.02, gamma = 1,
- * sigma = 0.1, eps = 1e-3, 20 iterations, one level, K on the tensor cores (bf16x3). */
+ * sigma = 0.1, eps = 1e-3, 20 iterations, one level, K by FP32 DFT products (LDDMM_K_FP32), fp32 storage, timeout 600 s. */
 int lddmm_default_params(lddmm_params* p, int nx, int ny, int nz);
 
 /* Create a context: validates p, allocates device buffers for all levels, copies I0

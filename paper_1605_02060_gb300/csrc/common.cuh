@@ -67,6 +67,19 @@ __device__ __forceinline__ float tri_sample(const float* __restrict__ f, const G
 __device__ __forceinline__ float ldf(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
 __device__ __forceinline__ void stf(float* p, float v) { *p = v; }
+// Loads issued where they are written (volatile asm is not moved by the compiler): used for
+// prefetches whose value is consumed several iterations later, which the compiler would
+// otherwise sink next to the use and so expose the full memory latency.
+__device__ __forceinline__ float ldf_now(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ldf_now(const __nv_bfloat16* p) {
+  unsigned short h;
+  asm volatile("ld.global.nc.u16 %0, [%1];" : "=h"(h) : "l"(p));
+  return __bfloat162float(__ushort_as_bfloat16(h));
+}
 __device__ __forceinline__ void stf(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
 
 template <typename T>

@@ -27,7 +27,7 @@ struct Hook {
 
 enum KernelId {
   KID_BACK_DISP = 0, KID_BACK_TERMS, KID_FWD_TERMS, KID_FWD_FLOW, KID_KX_FWD, KID_KY_FWD,
-  KID_KZ_SYM, KID_KZ_INV, KID_KY_INV, KID_KX_INV, KID_UPDATE, KID_COUNT
+  KID_KZ_SYM, KID_KZ_INV, KID_KY_INV, KID_KX_INV, KID_UPDATE, KID_EREG, KID_COUNT
 };
 
 // ---- flows (kernels_flow.cu) ----
@@ -42,12 +42,14 @@ void launch_flow_back(const Grid& g, const void* vj, const float* u_next, float*
 void launch_fwd_terms(const Grid& g, const float* u_cur, const void* I0, const float* J1j,
                       const float* Wj, float* b, float c, float ihx, float ihy, float ihz,
                       cudaStream_t s, int st);
-// Forward sweep step j: u_next = -dt v_j / h + u_cur(x - dt v_j / h) (u_cur == nullptr: id),
-// E_reg contribution of v_j; if last, J0_T = I0 o (id + u_next) and E_data.
+// Forward sweep step j: u_next = -dt v_j / h + u_cur(x - dt v_j / h) (u_cur == nullptr: id);
+// if last, J0_T = I0 o (id + u_next) and E_data.
 void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u_next,
-                     float dtx, float dty, float dtz, float alpha, float gamma, float ihx2,
-                     float ihy2, float ihz2, bool last, const void* I0, const void* I1,
+                     float dtx, float dty, float dtz, bool last, const void* I0, const void* I1,
                      const void* M, float* J0T, Acc* acc, cudaStream_t s, int st);
+// E_reg of all T fields v[T][3][N] into acc->e_reg (unscaled sum of |(gamma - alpha Lap_h) v|^2).
+void launch_ereg(const Grid& g, const void* v, int T, float alpha, float gamma, float ihx2,
+                 float ihy2, float ihz2, Acc* acc, cudaStream_t s, int st);
 // v_j <- v_j - eps (2 v_j - Kb), 3 components.
 void launch_update(const Grid& g, void* vj, const float* Kb, float eps, cudaStream_t s, int st);
 // Displacement of phi_{1,0} / phi_{0,1} only (flows without the residual), to refresh maps.

@@ -29,24 +29,69 @@ static inline dim3 grid3d(const Grid& g) { return dim3((g.nx + 31) / 32, (g.ny +
 static const dim3 kBlock3d(32, 8, 1);
 
 // --------------------------------------------------------------------------------------------
-// Backward sweep, part 1: displacement of phi_{j,1}.
-template <typename ST>
-__global__ void k_back_disp(Grid g, const ST* __restrict__ vj, const float* __restrict__ un,
-                            float* __restrict__ uc, float dtx, float dty, float dtz) {
-  int x, y, z, idx;
-  if (!voxel3d(g, x, y, z, idx)) return;
-  const float dx = dtx * ldf(vj + idx), dy = dty * ldf(vj + g.N + idx),
-              dz = dtz * ldf(vj + 2 * g.N + idx);
-  float ox = dx, oy = dy, oz = dz;
-  if (un) {
-    Tri w = tri_setup(g, (float)x + dx, (float)y + dy, (float)z + dz);
-    ox += tri_apply(un, w);
-    oy += tri_apply(un + g.N, w);
-    oz += tri_apply(un + 2 * g.N, w);
+// One semi-Lagrangian step of a map, marching ZC planes in z per thread:
+//   u_out(x) = s dt v_j(x)/h + u_in(x + s dt v_j(x)/h)   (u_in == nullptr: the identity),
+// s = +1 for phi_{j,1} (backward sweep) and s = -1 for phi_{j+1,0} (forward sweep).  A voxel
+// costs two dependent memory latencies (v_j, then the eight corners at the displaced point); the
+// velocity of plane z+1 is loaded before the corners of plane z are requested, so the two
+// overlap.  Consecutive planes also gather from overlapping cells, which L1 keeps.
+template <typename ST, int SGN, int ZC>
+__global__ void __launch_bounds__(256) k_disp_march(Grid g, const ST* __restrict__ vj,
+                                                    const float* __restrict__ uin,
+                                                    float* __restrict__ uout, float dtx,
+                                                    float dty, float dtz) {
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+  if (x >= g.nx || y >= g.ny) return;
+  const int z0 = blockIdx.z * ZC, z1 = min(z0 + ZC, g.nz);
+  const int plane = g.nx * g.ny;
+  int idx = (z0 * g.ny + y) * g.nx + x;
+  float a0 = ldf(vj + idx), a1 = ldf(vj + g.N + idx), a2 = ldf(vj + 2 * g.N + idx);
+  for (int z = z0; z < z1; ++z, idx += plane) {
+    float n0 = 0.f, n1 = 0.f, n2 = 0.f;
+    if (z + 1 < z1) {
+      n0 = ldf_now(vj + idx + plane);
+      n1 = ldf_now(vj + g.N + idx + plane);
+      n2 = ldf_now(vj + 2 * g.N + idx + plane);
+    }
+    const float dx = (float)SGN * (dtx * a0), dy = (float)SGN * (dty * a1),
+                dz = (float)SGN * (dtz * a2);
+    float ox = dx, oy = dy, oz = dz;
+    if (uin) {
+      const Tri w = tri_setup(g, (float)x + dx, (float)y + dy, (float)z + dz);
+      ox += tri_apply(uin, w);
+      oy += tri_apply(uin + g.N, w);
+      oz += tri_apply(uin + 2 * g.N, w);
+    }
+    uout[idx] = ox;
+    uout[g.N + idx] = oy;
+    uout[2 * g.N + idx] = oz;
+    a0 = n0;
+    a1 = n1;
+    a2 = n2;
   }
-  uc[idx] = ox;
-  uc[g.N + idx] = oy;
-  uc[2 * g.N + idx] = oz;
+}
+
+// Four planes per thread: deep enough to overlap the two latencies, short enough that the grid
+// (ceil(nz/4) blocks along z) fills the GPU several times over.
+constexpr int kFlowZ = 4;
+
+template <typename ST, int SGN>
+static void launch_disp_march(const Grid& g, const void* vj, const float* uin, float* uout,
+                              float dtx, float dty, float dtz, cudaStream_t s) {
+  const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + kFlowZ - 1) / kFlowZ);
+  k_disp_march<ST, SGN, kFlowZ><<<grid, kBlock3d, 0, s>>>(g, (const ST*)vj, uin, uout, dtx, dty,
+                                                          dtz);
+}
+
+static void disp_step(int sgn, const Grid& g, const void* vj, const float* uin, float* uout,
+                      float dtx, float dty, float dtz, cudaStream_t s, int st) {
+  if (sgn > 0) {
+    if (st) launch_disp_march<__nv_bfloat16, 1>(g, vj, uin, uout, dtx, dty, dtz, s);
+    else launch_disp_march<float, 1>(g, vj, uin, uout, dtx, dty, dtz, s);
+  } else {
+    if (st) launch_disp_march<__nv_bfloat16, -1>(g, vj, uin, uout, dtx, dty, dtz, s);
+    else launch_disp_march<float, -1>(g, vj, uin, uout, dtx, dty, dtz, s);
+  }
 }
 
 // det(I + Du) at voxel (x,y,z) with the one-sided/central stencil.
@@ -92,8 +137,7 @@ void launch_flow_back(const Grid& g, const void* vj, const float* u_next, float*
                       const void* I1, const void* M, float* J1j, float* Wj, float dtx,
                       float dty, float dtz, Acc* acc, cudaStream_t s, const Hook& hook, int st) {
   hook(KID_BACK_DISP, 0);
-  if (st) k_back_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, (const __nv_bfloat16*)vj, u_next, u_cur, dtx, dty, dtz);
-  else k_back_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, (const float*)vj, u_next, u_cur, dtx, dty, dtz);
+  disp_step(+1, g, vj, u_next, u_cur, dtx, dty, dtz, s, st);
   hook(KID_BACK_DISP, 1);
   hook(KID_BACK_TERMS, 0);
   if (st)
@@ -107,8 +151,7 @@ void launch_flow_back(const Grid& g, const void* vj, const float* u_next, float*
 
 void launch_flow_only_back(const Grid& g, const void* vj, const float* u_next, float* u_cur,
                            float dtx, float dty, float dtz, cudaStream_t s, int st) {
-  if (st) k_back_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, (const __nv_bfloat16*)vj, u_next, u_cur, dtx, dty, dtz);
-  else k_back_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, (const float*)vj, u_next, u_cur, dtx, dty, dtz);
+  disp_step(+1, g, vj, u_next, u_cur, dtx, dty, dtz, s, st);
 }
 
 // --------------------------------------------------------------------------------------------
@@ -180,17 +223,16 @@ void launch_fwd_terms(const Grid& g, const float* u_cur, const void* I0, const f
                                                ihz);
 }
 
-// Forward sweep, flow: u_next = -dt v_j/h + u_cur(x - dt v_j/h); E_reg of v_j (periodic
-// 7-point (gamma - alpha Lap_h) v_j, summed over components); at the last step J0_T and E_data.
+// Forward sweep, flow: u_next = -dt v_j/h + u_cur(x - dt v_j/h); at the last step J0_T and
+// E_data.
 template <typename ST>
 __global__ void k_fwd_flow(Grid g, const ST* __restrict__ vj, const float* __restrict__ uc,
-                           float* __restrict__ un, float dtx, float dty, float dtz, float alpha,
-                           float gamma, float ihx2, float ihy2, float ihz2, int last,
+                           float* __restrict__ un, float dtx, float dty, float dtz, int last,
                            const ST* __restrict__ I0, const ST* __restrict__ I1,
                            const ST* __restrict__ M, float* __restrict__ J0T, Acc* acc) {
   int x, y, z, idx;
   const bool in = voxel3d(g, x, y, z, idx);
-  float ereg = 0.f, edata = 0.f;
+  float edata = 0.f;
   if (in) {
     const float v0 = ldf(vj + idx), v1 = ldf(vj + g.N + idx), v2 = ldf(vj + 2 * g.N + idx);
     const float dx = dtx * v0, dy = dty * v1, dz = dtz * v2;
@@ -204,21 +246,6 @@ __global__ void k_fwd_flow(Grid g, const ST* __restrict__ vj, const float* __res
     un[idx] = ox;
     un[g.N + idx] = oy;
     un[2 * g.N + idx] = oz;
-    // regulariser: periodic neighbours
-    const int xm = (x == 0 ? g.nx - 1 : -1), xp = (x == g.nx - 1 ? -(g.nx - 1) : 1);
-    const int sy = g.nx, sz = g.nx * g.ny;
-    const int ym = (y == 0 ? (g.ny - 1) * sy : -sy), yp = (y == g.ny - 1 ? -(g.ny - 1) * sy : sy);
-    const int zm = (z == 0 ? (g.nz - 1) * sz : -sz), zp = (z == g.nz - 1 ? -(g.nz - 1) * sz : sz);
-    const float vc[3] = {v0, v1, v2};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const ST* p = vj + c * g.N + idx;
-      const float lap = (ldf(p + xm) - 2.f * vc[c] + ldf(p + xp)) * ihx2 +
-                        (ldf(p + ym) - 2.f * vc[c] + ldf(p + yp)) * ihy2 +
-                        (ldf(p + zm) - 2.f * vc[c] + ldf(p + zp)) * ihz2;
-      const float Lv = gamma * vc[c] - alpha * lap;
-      ereg = fmaf(Lv, Lv, ereg);
-    }
     if (last) {
       const float j0 = tri_apply_t(I0, tri_setup(g, (float)x + ox, (float)y + oy, (float)z + oz));
       J0T[idx] = j0;
@@ -226,52 +253,175 @@ __global__ void k_fwd_flow(Grid g, const ST* __restrict__ vj, const float* __res
       edata = ldf(M + idx) * r * r;
     }
   }
-  block_sum_f_atomic(ereg, &acc->e_reg);
-  if (last) {
-    __syncthreads();
-    block_sum_f_atomic(edata, &acc->e_data);
-  }
+  if (last) block_sum_f_atomic(edata, &acc->e_data);
 }
 
 void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u_next,
-                     float dtx, float dty, float dtz, float alpha, float gamma, float ihx2,
-                     float ihy2, float ihz2, bool last, const void* I0, const void* I1,
+                     float dtx, float dty, float dtz, bool last, const void* I0, const void* I1,
                      const void* M, float* J0T, Acc* acc, cudaStream_t s, int st) {
+  if (!last) {
+    disp_step(-1, g, vj, u_cur, u_next, dtx, dty, dtz, s, st);
+    return;
+  }
   if (st)
     k_fwd_flow<<<grid3d(g), kBlock3d, 0, s>>>(
-        g, (const __nv_bfloat16*)vj, u_cur, u_next, dtx, dty, dtz, alpha, gamma, ihx2, ihy2, ihz2,
-        last ? 1 : 0, (const __nv_bfloat16*)I0, (const __nv_bfloat16*)I1, (const __nv_bfloat16*)M,
-        J0T, acc);
+        g, (const __nv_bfloat16*)vj, u_cur, u_next, dtx, dty, dtz, last ? 1 : 0,
+        (const __nv_bfloat16*)I0, (const __nv_bfloat16*)I1, (const __nv_bfloat16*)M, J0T, acc);
   else
     k_fwd_flow<<<grid3d(g), kBlock3d, 0, s>>>(g, (const float*)vj, u_cur, u_next, dtx, dty, dtz,
-                                              alpha, gamma, ihx2, ihy2, ihz2, last ? 1 : 0,
-                                              (const float*)I0, (const float*)I1,
+                                              last ? 1 : 0, (const float*)I0, (const float*)I1,
                                               (const float*)M, J0T, acc);
 }
 
-template <typename ST>
-__global__ void k_fwd_disp(Grid g, const ST* __restrict__ vj, const float* __restrict__ uc,
-                           float* __restrict__ un, float dtx, float dty, float dtz) {
-  int x, y, z, idx;
-  if (!voxel3d(g, x, y, z, idx)) return;
-  const float dx = dtx * ldf(vj + idx), dy = dty * ldf(vj + g.N + idx),
-              dz = dtz * ldf(vj + 2 * g.N + idx);
-  float ox = -dx, oy = -dy, oz = -dz;
-  if (uc) {
-    Tri w = tri_setup(g, (float)x - dx, (float)y - dy, (float)z - dz);
-    ox += tri_apply(uc, w);
-    oy += tri_apply(uc + g.N, w);
-    oz += tri_apply(uc + 2 * g.N, w);
+// --------------------------------------------------------------------------------------------
+// Regulariser energy of all T velocity fields (the first term of the energy, §2.4):
+//   sum_j sum_c sum_x ((gamma - alpha Lap_h) v_{j,c})(x)^2,  Lap_h the periodic 7-point stencil.
+// The 3T components are independent scalar fields.  A thread owns VEC consecutive x of one row
+// and marches kEregZ planes in z, keeping the planes z-1, z, z+1 of its VEC voxels in registers;
+// threads run over the (x/VEC, y) slots of a plane in order, so a warp holds adjacent vectors of
+// a row and takes the x-neighbours across vectors from the neighbouring lanes by shuffle (the
+// lanes at a warp or row edge load them).  Rows y+-1 are loaded (L1 hits: they are other
+// threads' centres).  The loads for plane z+1 are issued before plane z is evaluated.  The
+// stencil is ALU work (about 12 FP32 operations a voxel), so the vector width cuts the
+// per-voxel instruction count; a field is read once from DRAM.  Per-plane partial sums are
+// FP32, accumulated with compensated (Kahan) addition per thread; the block total goes to FP64.
+constexpr int kEregZ = 16;
+
+template <int VEC>
+__device__ __forceinline__ void ldvec(const float* p, float (&o)[VEC]) {
+  if constexpr (VEC == 4) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) o[k] = __ldg(p + k);
   }
-  un[idx] = ox;
-  un[g.N + idx] = oy;
-  un[2 * g.N + idx] = oz;
+}
+template <int VEC>
+__device__ __forceinline__ void ldvec(const __nv_bfloat16* p, float (&o)[VEC]) {
+  if constexpr (VEC == 4) {
+    const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+    const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&q.x);
+    const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&q.y);
+    o[0] = __low2float(lo); o[1] = __high2float(lo);
+    o[2] = __low2float(hi); o[3] = __high2float(hi);
+  } else {
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) o[k] = ldf(p + k);
+  }
+}
+
+template <typename ST, int VEC>
+__global__ void __launch_bounds__(256) k_ereg(Grid g, const ST* __restrict__ v, int nfield,
+                                              float alpha, float gamma, float ihx2, float ihy2,
+                                              float ihz2, Acc* acc) {
+  const int nxv = g.nx / VEC, slots = nxv * g.ny;
+  const int sl = blockIdx.x * 256 + threadIdx.x, lane = threadIdx.x & 31;
+  const bool in = sl < slots;
+  const int y = in ? sl / nxv : 0, xv = in ? sl - y * nxv : 0, x0 = xv * VEC;
+  const int ym = y == 0 ? g.ny - 1 : y - 1, yp = y + 1 == g.ny ? 0 : y + 1;
+  const bool lw = lane > 0 && xv > 0;            // lane - 1 holds the vector on the left
+  const bool rw = lane < 31 && xv + 1 < nxv;     // lane + 1 holds the vector on the right
+  const int xl = x0 == 0 ? g.nx - 1 : x0 - 1, xr = x0 + VEC == g.nx ? 0 : x0 + VEC;
+  const int oc = y * g.nx + x0, oym = ym * g.nx + x0, oyp = yp * g.nx + x0;
+  const int ol = y * g.nx + xl, orr = y * g.nx + xr;
+  const int nzc = (g.nz + kEregZ - 1) / kEregZ;
+  const int64_t plane = (int64_t)g.nx * g.ny;
+  float sum = 0.f, comp = 0.f;
+  for (int q = blockIdx.y; q < nzc * nfield; q += gridDim.y) {
+    const int f = q / nzc, z0 = (q - f * nzc) * kEregZ;
+    const int z1 = min(z0 + kEregZ, g.nz);
+    const ST* fb = v + (int64_t)f * g.N;
+    auto P = [&](int z) -> const ST* {
+      z = z < 0 ? z + g.nz : (z >= g.nz ? z - g.nz : z);
+      return fb + (int64_t)z * plane;
+    };
+    float prv[VEC], cur[VEC], nxt[VEC], am[VEC], bp[VEC];
+    float hl = 0.f, hr = 0.f;
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) prv[k] = cur[k] = nxt[k] = am[k] = bp[k] = 0.f;
+    if (in) {
+      ldvec<VEC>(P(z0 - 1) + oc, prv);
+      ldvec<VEC>(P(z0) + oc, cur);
+      ldvec<VEC>(P(z0 + 1) + oc, nxt);
+      const ST* p0 = P(z0);
+      ldvec<VEC>(p0 + oym, am);
+      ldvec<VEC>(p0 + oyp, bp);
+      if (!lw) hl = ldf(p0 + ol);
+      if (!rw) hr = ldf(p0 + orr);
+    }
+    for (int z = z0; z < z1; ++z) {
+      // loads for the next plane: centre of z + 2, neighbours of z + 1
+      float nn[VEC], am2[VEC], bp2[VEC];
+      float hl2 = 0.f, hr2 = 0.f;
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) nn[k] = am2[k] = bp2[k] = 0.f;
+      if (in && z + 1 < z1) {
+        ldvec<VEC>(P(z + 2) + oc, nn);
+        const ST* p1 = P(z + 1);
+        ldvec<VEC>(p1 + oym, am2);
+        ldvec<VEC>(p1 + oyp, bp2);
+        if (!lw) hl2 = ldf(p1 + ol);
+        if (!rw) hr2 = ldf(p1 + orr);
+      }
+      const float fromL = __shfl_up_sync(0xffffffffu, cur[VEC - 1], 1);
+      const float fromR = __shfl_down_sync(0xffffffffu, cur[0], 1);
+      if (in) {
+        float e = 0.f;
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+          const float l = k > 0 ? cur[k - 1] : (lw ? fromL : hl);
+          const float r = k + 1 < VEC ? cur[k + 1] : (rw ? fromR : hr);
+          const float c = cur[k];
+          const float lap = fmaf(-2.f, c, l + r) * ihx2 + fmaf(-2.f, c, am[k] + bp[k]) * ihy2 +
+                            fmaf(-2.f, c, prv[k] + nxt[k]) * ihz2;
+          const float Lv = fmaf(-alpha, lap, gamma * c);
+          e = fmaf(Lv, Lv, e);
+        }
+        const float yk = e - comp;
+        const float tt = sum + yk;
+        comp = (tt - sum) - yk;
+        sum = tt;
+      }
+#pragma unroll
+      for (int k = 0; k < VEC; ++k) {
+        prv[k] = cur[k];
+        cur[k] = nxt[k];
+        nxt[k] = nn[k];
+        am[k] = am2[k];
+        bp[k] = bp2[k];
+      }
+      hl = hl2;
+      hr = hr2;
+    }
+  }
+  block_sum_f_atomic(sum, &acc->e_reg);
+}
+
+void launch_ereg(const Grid& g, const void* v, int T, float alpha, float gamma, float ihx2,
+                 float ihy2, float ihz2, Acc* acc, cudaStream_t s, int st) {
+  // 4-wide vectors when every row starts on a vector boundary (the field bases are then aligned
+  // too: N is a multiple of nx and the buffer comes from cudaMalloc)
+  const bool v4 = g.nx % 4 == 0 && ((uintptr_t)v % 16) == 0;
+  const int vec = v4 ? 4 : 1;
+  const int64_t slots = (int64_t)(g.nx / vec) * g.ny;
+  const int nzc = (g.nz + kEregZ - 1) / kEregZ;
+  const int64_t nq = (int64_t)nzc * 3 * T;
+  const dim3 grid((unsigned)((slots + 255) / 256), (unsigned)(nq < 65535 ? nq : 65535));
+  if (st) {
+    const __nv_bfloat16* p = (const __nv_bfloat16*)v;
+    if (v4) k_ereg<__nv_bfloat16, 4><<<grid, 256, 0, s>>>(g, p, 3 * T, alpha, gamma, ihx2, ihy2, ihz2, acc);
+    else k_ereg<__nv_bfloat16, 1><<<grid, 256, 0, s>>>(g, p, 3 * T, alpha, gamma, ihx2, ihy2, ihz2, acc);
+  } else {
+    const float* p = (const float*)v;
+    if (v4) k_ereg<float, 4><<<grid, 256, 0, s>>>(g, p, 3 * T, alpha, gamma, ihx2, ihy2, ihz2, acc);
+    else k_ereg<float, 1><<<grid, 256, 0, s>>>(g, p, 3 * T, alpha, gamma, ihx2, ihy2, ihz2, acc);
+  }
 }
 
 void launch_flow_only_fwd(const Grid& g, const void* vj, const float* u_cur, float* u_next,
                           float dtx, float dty, float dtz, cudaStream_t s, int st) {
-  if (st) k_fwd_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, (const __nv_bfloat16*)vj, u_cur, u_next, dtx, dty, dtz);
-  else k_fwd_disp<<<grid3d(g), kBlock3d, 0, s>>>(g, (const float*)vj, u_cur, u_next, dtx, dty, dtz);
+  disp_step(-1, g, vj, u_cur, u_next, dtx, dty, dtz, s, st);
 }
 
 // --------------------------------------------------------------------------------------------

@@ -141,8 +141,8 @@ Hook hook_of(lddmm_ctx* ctx) {
 
 const char* kernel_name(int kid) {
   static const char* names[KID_COUNT] = {"flow_back_disp", "flow_back_terms", "fwd_residual",
-                                         "fwd_flow_ereg", "K_x_fwd", "K_y_fwd", "K_z_symbol",
-                                         "K_z_inv", "K_y_inv", "K_x_inv_update", "update"};
+                                         "fwd_flow", "K_x_fwd", "K_y_fwd", "K_z_symbol",
+                                         "K_z_inv", "K_y_inv", "K_x_inv_update", "update", "ereg"};
   return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 
@@ -318,6 +318,11 @@ int run_step(lddmm_ctx* ctx) {
     pb ^= 1;
   }
   ctx->u01 = un;
+  // E_reg of the velocity at the start of the iteration (before the forward sweep updates it)
+  hk(KID_EREG, 0);
+  launch_ereg(g, ctx->v, T, ctx->p.alpha, ctx->p.gamma, 1.0f / (L.hx * L.hx),
+              1.0f / (L.hy * L.hy), 1.0f / (L.hz * L.hz), ctx->acc, s, ctx->st);
+  hk(KID_EREG, 1);
   // forward sweep j = 0 .. T-1 with smoothing and update
   const float c = 2.0f / (ctx->p.sigma * ctx->p.sigma);
   const float* uc = nullptr;
@@ -330,9 +335,8 @@ int run_step(lddmm_ctx* ctx) {
     hk(KID_FWD_TERMS, 1);
     float* unx = ctx->uF[pf];
     hk(KID_FWD_FLOW, 0);
-    launch_fwd_flow(g, vj, uc, unx, dtx, dty, dtz, ctx->p.alpha, ctx->p.gamma,
-                    1.0f / (L.hx * L.hx), 1.0f / (L.hy * L.hy), 1.0f / (L.hz * L.hz), j == T - 1,
-                    L.I0, L.I1, L.M, ctx->J0T, ctx->acc, s, ctx->st);
+    launch_fwd_flow(g, vj, uc, unx, dtx, dty, dtz, j == T - 1, L.I0, L.I1, L.M, ctx->J0T,
+                    ctx->acc, s, ctx->st);
     hk(KID_FWD_FLOW, 1);
     // K b_j and the update v_j <- v_j - eps (2 v_j - K b_j): fused into the last DFT pass for
     // float storage, a separate pass for bf16 storage
@@ -374,14 +378,14 @@ int refresh_maps(lddmm_ctx* ctx, bool energy) {
     pb ^= 1;
   }
   ctx->u01 = un;
+  launch_ereg(g, ctx->v, T, ctx->p.alpha, ctx->p.gamma, 1.0f / (L.hx * L.hx),
+              1.0f / (L.hy * L.hy), 1.0f / (L.hz * L.hz), ctx->acc, s, ctx->st);
   const float* uc = nullptr;
   int pf = 0;
   for (int j = 0; j < T; ++j) {
     float* unx = ctx->uF[pf];
-    launch_fwd_flow(g, vptr(ctx, j, N), uc, unx, dtx, dty, dtz, ctx->p.alpha,
-                    ctx->p.gamma, 1.0f / (L.hx * L.hx), 1.0f / (L.hy * L.hy),
-                    1.0f / (L.hz * L.hz), j == T - 1, L.I0, L.I1, L.M, ctx->J0T, ctx->acc, s,
-                    ctx->st);
+    launch_fwd_flow(g, vptr(ctx, j, N), uc, unx, dtx, dty, dtz, j == T - 1, L.I0, L.I1, L.M,
+                    ctx->J0T, ctx->acc, s, ctx->st);
     uc = unx;
     pf ^= 1;
   }
@@ -816,14 +820,14 @@ int lddmm_energy_grad(lddmm_ctx* ctx, const float* v, float* grad, double* E) {
   // forward sweep (energy, u_j kept or checkpointed)
   if ((rc = reset_acc(ctx))) return rc;
   CK(cudaMemsetAsync(slot_of(0), 0, F * sizeof(float), s));
+  launch_ereg(g, ctx->v, T, ctx->p.alpha, ctx->p.gamma, ihx2, ihy2, ihz2, ctx->acc, s, 0);
   const float* uc = nullptr;
   int pf = 0;
   for (int j = 0; j < T; ++j) {
     const bool keep = !ckpt || j + 1 == T || (j + 1) % c == 0;
     float* unx = keep ? slot_of(j + 1) : ctx->uF[pf];
-    launch_fwd_flow(g, ctx->v + (int64_t)j * F, uc, unx, dtx, dty, dtz, ctx->p.alpha,
-                    ctx->p.gamma, ihx2, ihy2, ihz2, j == T - 1, L.I0, L.I1, L.M, ctx->J0T,
-                    ctx->acc, s, 0);
+    launch_fwd_flow(g, ctx->v + (int64_t)j * F, uc, unx, dtx, dty, dtz, j == T - 1, L.I0, L.I1,
+                    L.M, ctx->J0T, ctx->acc, s, 0);
     uc = unx;
     if (!keep) pf ^= 1;
   }
