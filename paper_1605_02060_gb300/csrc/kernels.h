@@ -91,6 +91,12 @@ struct KPlan {
   // tensor-core operand tables per axis (x, y, z) and direction (0 forward, 1 inverse):
   // nk = Npad/16 k-steps, each [hi | lo] bf16 blocks of Npad x 16 in K-major core-matrix order
   uint16_t* tc[3][2];
+  // x axis with 256 < nx <= 264 (the TMA pass): the first 256 output columns on the tensor
+  // cores (tables as above with 256 rows), the last xtw = nx - 256 columns in FP32 on the CUDA
+  // cores from xtail[dir] = B(k, 256 + j) as float [Kpad][8] (zero beyond nx)
+  uint16_t* tcx[2];
+  float* xtail[2];
+  int xtw;
   int* err;  // device flag set by a tensor-core kernel whose bounded wait timed out
 };
 // Build device tables for one grid (allocates; free with kplan_destroy).

@@ -55,18 +55,20 @@ static float bf16_to_f(uint16_t b) {
   return f;
 }
 
-// Tensor-core operand table: B(k, n) = R[n][k] (forward) or R[k][n] (inverse), zero-padded to
-// Npad = ceil16(n); per 16-wide k-step a bf16 hi block then a bf16 lo block (R = hi + lo), each
-// Npad rows x 16 k in the K-major no-swizzle core-matrix order the MMA descriptors expect:
+// Tensor-core operand table: B(k, n) = R[n][k] (forward) or R[k][n] (inverse) for the output
+// columns n < rows (rows a multiple of 16; zero for n >= n_len), k zero-padded to ceil16(n_len);
+// per 16-wide k-step a bf16 hi block then a bf16 lo block (B = hi + lo), each rows x 16 k in the
+// K-major no-swizzle core-matrix order the MMA descriptors expect:
 // element (row, kk) at byte (kk/8)*128 + (row/8)*256 + (row%8)*16 + (kk%8)*2.
-static void tc_table(const std::vector<float>& R, int n, bool inverse, std::vector<uint16_t>& t) {
-  const int Npad = (n + 15) / 16 * 16, nk = Npad / 16;
-  const size_t block = (size_t)Npad * 16;  // elements per hi (or lo) block
+static void tc_table(const std::vector<float>& R, int n, bool inverse, int rows,
+                     std::vector<uint16_t>& t) {
+  const int Kpad = (n + 15) / 16 * 16, nk = Kpad / 16;
+  const size_t block = (size_t)rows * 16;  // elements per hi (or lo) block
   t.assign((size_t)nk * 2 * block, 0);
   for (int s = 0; s < nk; ++s) {
     uint16_t* hi = t.data() + (size_t)s * 2 * block;
     uint16_t* lo = hi + block;
-    for (int row = 0; row < Npad; ++row)
+    for (int row = 0; row < rows; ++row)
       for (int kk = 0; kk < 16; ++kk) {
         const int k = s * 16 + kk;
         float b = 0.f;
@@ -79,6 +81,17 @@ static void tc_table(const std::vector<float>& R, int n, bool inverse, std::vect
         lo[off] = bl;
       }
   }
+}
+
+// FP32 tail columns 256..n-1 of B as [Kpad][8] (zero beyond n and for j >= n - 256).
+static void tail_table(const std::vector<float>& R, int n, bool inverse, std::vector<float>& t) {
+  const int Kpad = (n + 15) / 16 * 16;
+  t.assign((size_t)Kpad * 8, 0.f);
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < 8 && 256 + j < n; ++j) {
+      const int col = 256 + j;
+      t[(size_t)k * 8 + j] = inverse ? R[(size_t)k * n + col] : R[(size_t)col * n + k];
+    }
 }
 
 template <typename T>
@@ -105,8 +118,19 @@ cudaError_t kplan_create(KPlan* kp, int nx, int ny, int nz, float hx, float hy, 
     if ((e = upload(ls[d], lam)) != cudaSuccess) return e;
     for (int dir = 0; dir < 2; ++dir) {
       std::vector<uint16_t> t;
-      tc_table(R, n[d], dir == 1, t);
+      tc_table(R, n[d], dir == 1, (n[d] + 15) / 16 * 16, t);
       if ((e = upload(&kp->tc[d][dir], t)) != cudaSuccess) return e;
+    }
+    if (d == 0 && nx > 256 && nx <= 264) {
+      kp->xtw = nx - 256;
+      for (int dir = 0; dir < 2; ++dir) {
+        std::vector<uint16_t> t;
+        tc_table(R, nx, dir == 1, 256, t);
+        if ((e = upload(&kp->tcx[dir], t)) != cudaSuccess) return e;
+        std::vector<float> tt;
+        tail_table(R, nx, dir == 1, tt);
+        if ((e = upload(&kp->xtail[dir], tt)) != cudaSuccess) return e;
+      }
     }
   }
   cudaError_t e = cudaMalloc((void**)&kp->err, sizeof(int));
@@ -121,6 +145,10 @@ void kplan_destroy(KPlan* kp) {
   for (int d = 0; d < 3; ++d)
     for (int dir = 0; dir < 2; ++dir)
       if (kp->tc[d][dir]) cudaFree(kp->tc[d][dir]);
+  for (int dir = 0; dir < 2; ++dir) {
+    if (kp->tcx[dir]) cudaFree(kp->tcx[dir]);
+    if (kp->xtail[dir]) cudaFree(kp->xtail[dir]);
+  }
   *kp = KPlan{};
 }
 

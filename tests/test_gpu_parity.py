@@ -56,7 +56,10 @@ PROD = K_MODES[MODES[-1]][0]   # the mode the benchmark runs
 @pytest.mark.parametrize("shape,h,alpha,gamma", [((32, 32, 32), (1, 1, 1), 0.02, 1.0),
                                                  ((29, 20, 33), (4, 4, 4), 0.02, 1.0),
                                                  ((9, 11, 17), (1.0, 2.0, 0.5), 0.5, 1.7),
-                                                 ((2, 3, 5), (1, 1, 1), 1.0, 1.0)])
+                                                 ((2, 3, 5), (1, 1, 1), 1.0, 1.0),
+                                                 # x lengths past 256: FP32 tail columns
+                                                 ((6, 5, 264), (1, 1, 1), 0.02, 1.0),
+                                                 ((4, 7, 260), (1, 1, 1), 0.3, 1.2)])
 def test_K_matches_oracle(L, O, mode, shape, h, alpha, gamma):
     code, tol = K_MODES[mode]
     rng = np.random.default_rng(1)
@@ -109,7 +112,8 @@ def _pair_small(synth, shape=(32, 32, 32)):
 
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("shape,T,h", [((32, 32, 32), 10, (1, 1, 1)),
-                                       ((20, 17, 23), 3, (1.0, 1.25, 0.8))])
+                                       ((20, 17, 23), 3, (1.0, 1.25, 0.8)),
+                                       ((8, 10, 260), 3, (1, 1, 1))])
 def test_one_step_matches_oracle(L, O, synth, mode, shape, T, h):
     Z, Y, X = shape
     pair = synth.ellipsoid_pair(shape=shape, centre=((X - 1) / 2, (Y - 1) / 2, (Z - 1) / 2),
