@@ -55,7 +55,7 @@ def _csrc_hash():
 
 # Algorithmic bytes (or flops) per voxel for one launch of each kernel (fp32 storage);
 # the derivation is in the design notes: each field is read or written once per launch.
-def algorithmic(kernel, N, dims, kmode, T=10):
+def algorithmic(kernel, N, dims, kmode, T=10, peaks=None):
     X, Y, Z = dims
     B = {"flow_back_disp": 36, "flow_back_terms": 28, "fwd_residual": 36,
          "fwd_flow": 36, "update": 36}
@@ -65,8 +65,20 @@ def algorithmic(kernel, N, dims, kmode, T=10):
         return {"bound": "hbm", "bytes": 12 * T * N}
     L = {"K_x_fwd": X, "K_x_inv_update": X, "K_y_fwd": Y, "K_y_inv": Y, "K_z_symbol": Z,
          "K_z_inv": Z}[kernel]
-    flops = 2.0 * L * 3 * N          # dense real DFT along one axis, 3 components
-    return {"bound": "alu" if kmode == 0 else "tensor", "flops": flops, "bytes": 24 * N}
+    # one DFT pass over 3 components: field in and out (24 B/voxel; the fused update also reads
+    # and writes v: 36 B/voxel); the mathematical product is 2 L flops per output value, which
+    # the bf16x3 tensor-core form computes three times (hi*hi + hi*lo + lo*hi)
+    nbytes = (36 if kernel == "K_x_inv_update" else 24) * N
+    flops = 2.0 * L * 3 * N
+    if kmode == 0:
+        return {"bound": "alu", "flops": flops, "bytes": nbytes}
+    hw_flops = flops * (3 if kmode == 1 else 1)
+    if peaks:
+        t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
+        t_tc = hw_flops / (peaks["bf16_tflops_sustained"] * 1e12)
+        if t_hbm >= t_tc:            # the bytes, not the tensor pipe, set this pass's floor
+            return {"bound": "hbm", "bytes": nbytes, "flops": flops}
+    return {"bound": "tensor", "flops": flops, "hw_flops": hw_flops, "bytes": nbytes}
 
 
 class ClockSampler:
@@ -271,7 +283,7 @@ def run_ours(args):
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     name, (nl, tot_ms) = dom
     avg_s = tot_ms / nl / 1000.0
-    alg = algorithmic(name, N, (X, Y, Z), args.kmode, T)
+    alg = algorithmic(name, N, (X, Y, Z), args.kmode, T, peaks)
     traffic = _traffic(name)
     if alg["bound"] == "hbm":
         achieved = alg["bytes"] / avg_s / 1e9

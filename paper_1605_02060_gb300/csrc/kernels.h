@@ -34,10 +34,14 @@ enum KernelId {
 // Velocity fields and images (vj, I0, I1, M) are stored as float (st = 0) or bf16 (st = 1);
 // displacements, J1, W, b and all arithmetic are float.
 // Backward sweep step j: u_cur = dt v_j / h + u_next(x + dt v_j / h)  (u_next == nullptr: id),
-// then J1_j = I1 o phi, W_j = (M o phi) det(I + Du_cur), min det into acc.
+// then J1_j = I1 o phi, W_j = (M o phi) det(I + Du_cur), min det into acc.  IM holds I1 and M
+// interleaved as pairs (launch_interleave).
 void launch_flow_back(const Grid& g, const void* vj, const float* u_next, float* u_cur,
-                      const void* I1, const void* M, float* J1j, float* Wj, float dtx,
-                      float dty, float dtz, Acc* acc, cudaStream_t s, const Hook& hook, int st);
+                      const void* IM, float* J1j, float* Wj, float dtx, float dty, float dtz,
+                      Acc* acc, cudaStream_t s, const Hook& hook, int st);
+// out[i] = (a[i], b[i]) as storage-type pairs.
+void launch_interleave(const void* a, const void* b, void* out, int64_t n, cudaStream_t s,
+                       int st);
 // Forward sweep step j: b = c W_j (J0_j - J1_j) grad J0_j / h,  J0_j = I0 o (id + u_cur).
 void launch_fwd_terms(const Grid& g, const float* u_cur, const void* I0, const float* J1j,
                       const float* Wj, float* b, float c, float ihx, float ihy, float ihz,

@@ -94,58 +94,141 @@ static void disp_step(int sgn, const Grid& g, const void* vj, const float* uin, 
   }
 }
 
-// det(I + Du) at voxel (x,y,z) with the one-sided/central stencil.
-__device__ __forceinline__ float jac_det(const Grid& g, const float* __restrict__ u, int idx,
-                                         int x, int y, int z) {
-  int lo[3], hi[3];
-  float inv[3];
-  fd_stencil(x, g.nx, 1, lo[0], hi[0], inv[0]);
-  fd_stencil(y, g.ny, g.nx, lo[1], hi[1], inv[1]);
-  fd_stencil(z, g.nz, g.nx * g.ny, lo[2], hi[2], inv[2]);
-  float D[3][3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const float* ud = u + d * g.N + idx;
-#pragma unroll
-    for (int e = 0; e < 3; ++e) D[d][e] = (__ldg(ud + hi[e]) - __ldg(ud + lo[e])) * inv[e];
-    D[d][d] += 1.0f;
-  }
-  return D[0][0] * (D[1][1] * D[2][2] - D[1][2] * D[2][1]) -
-         D[0][1] * (D[1][0] * D[2][2] - D[1][2] * D[2][0]) +
-         D[0][2] * (D[1][0] * D[2][1] - D[1][1] * D[2][0]);
+// Backward sweep, part 2: J1_j = I1 o phi_{j,1}, W_j = (M o phi_{j,1}) det D phi_{j,1}.
+// I1 and M are read as interleaved pairs (one 8-byte load per trilinear corner for fp32
+// storage).  A thread marches ZC planes in z, keeping u at z-1, z, z+1 (and the next plane, in
+// flight) in registers: the z-derivative of the map needs no loads, and the lookup position of
+// plane z+1 is known before plane z is finished.  The stencil is central inside and one-sided
+// at the faces, the trilinear lerps run x, then y, then z: the values equal those of a
+// one-voxel-per-thread evaluation.
+template <typename ST> struct Pair;
+template <> struct Pair<float> { typedef float2 T; };
+template <> struct Pair<__nv_bfloat16> { typedef __nv_bfloat162 T; };
+__device__ __forceinline__ float2 ldpair(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ldpair(const __nv_bfloat162* p) {
+  return __bfloat1622float2(__ldg(p));
 }
 
-// Backward sweep, part 2: J1_j = I1 o phi_{j,1}, W_j = (M o phi_{j,1}) det D phi_{j,1}.
-template <typename ST>
-__global__ void k_back_terms(Grid g, const float* __restrict__ uc, const ST* __restrict__ I1,
-                             const ST* __restrict__ M, float* __restrict__ J1j,
-                             float* __restrict__ Wj, Acc* acc) {
-  int x, y, z, idx;
-  const bool in = voxel3d(g, x, y, z, idx);
+template <typename PT>
+__device__ __forceinline__ float2 tri_apply_pair(const PT* __restrict__ f, const Tri& w) {
+  const PT* p = f + w.base;
+  const float2 c000 = ldpair(p), c001 = ldpair(p + w.sx);
+  const float2 c010 = ldpair(p + w.sy), c011 = ldpair(p + w.sy + w.sx);
+  const float2 c100 = ldpair(p + w.sz), c101 = ldpair(p + w.sz + w.sx);
+  const float2 c110 = ldpair(p + w.sz + w.sy), c111 = ldpair(p + w.sz + w.sy + w.sx);
+  float2 r;
+  {
+    const float a00 = c000.x + w.tx * (c001.x - c000.x), a01 = c010.x + w.tx * (c011.x - c010.x);
+    const float a10 = c100.x + w.tx * (c101.x - c100.x), a11 = c110.x + w.tx * (c111.x - c110.x);
+    const float b0 = a00 + w.ty * (a01 - a00), b1 = a10 + w.ty * (a11 - a10);
+    r.x = b0 + w.tz * (b1 - b0);
+  }
+  {
+    const float a00 = c000.y + w.tx * (c001.y - c000.y), a01 = c010.y + w.tx * (c011.y - c010.y);
+    const float a10 = c100.y + w.tx * (c101.y - c100.y), a11 = c110.y + w.tx * (c111.y - c110.y);
+    const float b0 = a00 + w.ty * (a01 - a00), b1 = a10 + w.ty * (a11 - a10);
+    r.y = b0 + w.tz * (b1 - b0);
+  }
+  return r;
+}
+
+template <typename ST, int ZC>
+__global__ void __launch_bounds__(256) k_back_terms_march(Grid g, const float* __restrict__ uc,
+                                                          const typename Pair<ST>::T* __restrict__ IM,
+                                                          float* __restrict__ J1j,
+                                                          float* __restrict__ Wj, Acc* acc) {
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+  const bool in = x < g.nx && y < g.ny;
   float dmin = 3.0e38f;
   if (in) {
-    const float det = jac_det(g, uc, idx, x, y, z);
-    Tri w = tri_setup(g, (float)x + uc[idx], (float)y + uc[g.N + idx], (float)z + uc[2 * g.N + idx]);
-    J1j[idx] = tri_apply_t(I1, w);
-    Wj[idx] = tri_apply_t(M, w) * det;
-    dmin = det;
+    const int z0 = blockIdx.z * ZC, z1 = min(z0 + ZC, g.nz);
+    const int plane = g.nx * g.ny, rowoff = y * g.nx;
+    // x and y stencils (central inside, one-sided at the faces)
+    const int xlo = x > 0 ? x - 1 : x, xhi = x < g.nx - 1 ? x + 1 : x;
+    const int ylo = y > 0 ? y - 1 : y, yhi = y < g.ny - 1 ? y + 1 : y;
+    const float ix = (x > 0 && x < g.nx - 1) ? 0.5f : 1.0f;
+    const float iy = (y > 0 && y < g.ny - 1) ? 0.5f : 1.0f;
+    auto ld3 = [&](int z, float* u) {
+      const int i = z * plane + rowoff + x;
+      u[0] = __ldg(uc + i); u[1] = __ldg(uc + g.N + i); u[2] = __ldg(uc + 2 * g.N + i);
+    };
+    float uP[3], uC[3], uN[3], uNN[3];
+    ld3(z0 > 0 ? z0 - 1 : z0, uP);
+    ld3(z0, uC);
+    ld3(z0 + 1 < g.nz ? z0 + 1 : z0, uN);
+    for (int z = z0; z < z1; ++z) {
+      // the plane after next, for the z-derivative of plane z + 1
+      const int zn = z + 2 < g.nz ? z + 2 : g.nz - 1;
+      if (z + 1 < z1) ld3(zn, uNN);
+      const int i = z * plane + rowoff + x;
+      float D[3][3];
+      const float* ucd[3] = {uc, uc + g.N, uc + 2 * g.N};
+      const float iz = (z > 0 && z < g.nz - 1) ? 0.5f : 1.0f;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float* q = ucd[d] + z * plane;
+        D[d][0] = (__ldg(q + rowoff + xhi) - __ldg(q + rowoff + xlo)) * ix;
+        D[d][1] = (__ldg(q + yhi * g.nx + x) - __ldg(q + ylo * g.nx + x)) * iy;
+        const float zh = z < g.nz - 1 ? uN[d] : uC[d], zl = z > 0 ? uP[d] : uC[d];
+        D[d][2] = (zh - zl) * iz;
+        D[d][d] += 1.0f;
+      }
+      const float det = D[0][0] * (D[1][1] * D[2][2] - D[1][2] * D[2][1]) -
+                        D[0][1] * (D[1][0] * D[2][2] - D[1][2] * D[2][0]) +
+                        D[0][2] * (D[1][0] * D[2][1] - D[1][1] * D[2][0]);
+      const Tri w = tri_setup(g, (float)x + uC[0], (float)y + uC[1], (float)z + uC[2]);
+      const float2 jm = tri_apply_pair(IM, w);
+      J1j[i] = jm.x;
+      Wj[i] = jm.y * det;
+      dmin = fminf(dmin, det);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        uP[d] = uC[d];
+        uC[d] = uN[d];
+        uN[d] = uNN[d];
+      }
+    }
   }
   block_min_atomic(dmin, &acc->min_det_ord);
 }
 
+template <typename ST>
+__global__ void k_interleave(const ST* __restrict__ a, const ST* __restrict__ b,
+                             typename Pair<ST>::T* __restrict__ out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    typename Pair<ST>::T v;
+    v.x = a[i];
+    v.y = b[i];
+    out[i] = v;
+  }
+}
+
+void launch_interleave(const void* a, const void* b, void* out, int64_t n, cudaStream_t s,
+                       int st) {
+  const int t = 256;
+  const int nb = (int)((n + t - 1) / t);
+  if (st)
+    k_interleave<<<nb, t, 0, s>>>((const __nv_bfloat16*)a, (const __nv_bfloat16*)b,
+                                  (__nv_bfloat162*)out, n);
+  else
+    k_interleave<<<nb, t, 0, s>>>((const float*)a, (const float*)b, (float2*)out, n);
+}
+
 void launch_flow_back(const Grid& g, const void* vj, const float* u_next, float* u_cur,
-                      const void* I1, const void* M, float* J1j, float* Wj, float dtx,
-                      float dty, float dtz, Acc* acc, cudaStream_t s, const Hook& hook, int st) {
+                      const void* IM, float* J1j, float* Wj, float dtx, float dty, float dtz,
+                      Acc* acc, cudaStream_t s, const Hook& hook, int st) {
   hook(KID_BACK_DISP, 0);
   disp_step(+1, g, vj, u_next, u_cur, dtx, dty, dtz, s, st);
   hook(KID_BACK_DISP, 1);
   hook(KID_BACK_TERMS, 0);
+  const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + kFlowZ - 1) / kFlowZ);
   if (st)
-    k_back_terms<<<grid3d(g), kBlock3d, 0, s>>>(g, u_cur, (const __nv_bfloat16*)I1,
-                                                (const __nv_bfloat16*)M, J1j, Wj, acc);
+    k_back_terms_march<__nv_bfloat16, kFlowZ><<<grid, kBlock3d, 0, s>>>(
+        g, u_cur, (const __nv_bfloat162*)IM, J1j, Wj, acc);
   else
-    k_back_terms<<<grid3d(g), kBlock3d, 0, s>>>(g, u_cur, (const float*)I1, (const float*)M, J1j,
-                                                Wj, acc);
+    k_back_terms_march<float, kFlowZ><<<grid, kBlock3d, 0, s>>>(g, u_cur, (const float2*)IM, J1j,
+                                                                Wj, acc);
   hook(KID_BACK_TERMS, 1);
 }
 

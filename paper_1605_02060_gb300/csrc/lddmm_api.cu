@@ -24,6 +24,7 @@ struct Level {
   int factor;
   float hx, hy, hz;
   float *I0 = nullptr, *I1 = nullptr, *M = nullptr;
+  float* IM = nullptr;   // I1 and M interleaved as pairs (backward-sweep lookups)
   KPlan kp{};
 };
 
@@ -230,6 +231,7 @@ int load_images(lddmm_ctx* ctx, const float* I0, const float* I1, const float* M
     launch_downsample(F.g, L.g, L.factor, s1, L.I1, ctx->stream, ctx->st);
     launch_downsample(F.g, L.g, L.factor, s2, L.M, ctx->stream, ctx->st);
   }
+  for (Level& L : ctx->levels) launch_interleave(L.I1, L.M, L.IM, L.g.N, ctx->stream, ctx->st);
   CK(cudaGetLastError());
   ctx->maps_valid = false;
   ctx->j0_valid = false;
@@ -238,7 +240,7 @@ int load_images(lddmm_ctx* ctx, const float* I0, const float* I1, const float* M
 
 void release(lddmm_ctx* ctx) {
   for (Level& L : ctx->levels) {
-    cudaFree(L.I0); cudaFree(L.I1); cudaFree(L.M);
+    cudaFree(L.I0); cudaFree(L.I1); cudaFree(L.M); cudaFree(L.IM);
     kplan_destroy(&L.kp);
   }
   void* ps2[] = {ctx->uall, ctx->gA, ctx->gB, ctx->seg};
@@ -312,7 +314,7 @@ int run_step(lddmm_ctx* ctx) {
   int pb = 0;
   for (int j = T - 1; j >= 0; --j) {
     float* uc = ctx->uB[pb];
-    launch_flow_back(g, vptr(ctx, j, N), un, uc, L.I1, L.M, ctx->J1 + j * N, ctx->W + j * N, dtx,
+    launch_flow_back(g, vptr(ctx, j, N), un, uc, L.IM, ctx->J1 + j * N, ctx->W + j * N, dtx,
                      dty, dtz, ctx->acc, s, hk, ctx->st);
     un = uc;
     pb ^= 1;
@@ -526,6 +528,7 @@ int lddmm_create(const lddmm_params* p, const float* I0, const float* I1, const 
     Level& L = ctx->levels[l];
     const int64_t ie = (L.g.N * (int64_t)ctx->es + 3) / 4;   // image storage, in floats
     ok = A(dalloc(&L.I0, ie)) && A(dalloc(&L.I1, ie)) && A(dalloc(&L.M, ie)) &&
+         A(dalloc(&L.IM, 2 * ie)) &&
          A(kplan_create(&L.kp, L.g.nx, L.g.ny, L.g.nz, L.hx, L.hy, L.hz, p->alpha, p->gamma));
   }
   const int64_t ve = (T * 3 * N * (int64_t)ctx->es + 3) / 4;  // velocity storage, in floats
