@@ -259,6 +259,8 @@ def run_ours(args):
     extras = None
     if ws == 1 and not args.no_extras:
         extras = measure_extras(L, I0, I1, M, stream, dev)
+        if not args.no_warm_start:
+            extras["warm_start"] = measure_warm_start()
     # end to end through the public API with host buffers: every step copies the images in from
     # pinned host memory and reads the energy back
     h0 = torch.from_numpy(pair.I0).pin_memory()
@@ -384,6 +386,43 @@ def measure_extras(L, I0, I1, M, stream, dev):
     return out
 
 
+def measure_warm_start():
+    """Time to the plain method's energy with and without the learned warm start, at 32^3:
+    a 4-level encoder-decoder (16/32/64/128 channels) trained on the GPU by the library's own
+    kernels on 240 ellipsoid-union pairs (x8 mirror images) labelled by 60 plain iterations;
+    on 8 held-out pairs the warm start (prediction smoothed by gamma^2 K, scaled by the energy)
+    iterates until it reaches the energy of 60 plain iterations.  Wall times include context
+    creation, prediction and the start's energy evaluations."""
+    import numpy as np
+
+    from paper_1605_02060_gb300 import surrogate as SG
+    n, T, iters = 32, 10, 60
+    t0 = time.perf_counter()
+    X, Y = SG.label_pairs(SG.make_pairs(240, n, seed0=1000, amp_max=4.0), iters, T)
+    X, Y = SG.augment_flips(X, Y, T)
+    net = SG.UNet3D(n=n, batch=8, seed=0, out_scale=float(np.sqrt((Y ** 2).mean())))
+    SG.train(net, X, Y, epochs=6, lr=1e-3)
+    train_s = time.perf_counter() - t0
+    rows = []
+    for pr in SG.make_pairs(8, n, seed0=5000, amp_max=4.0):
+        _, E, _, _ = SG.run_plain(pr, iters, T)
+        it_p, wall_p, dice_p = SG.run_plain_timed(pr, E[-1], 2 * iters, T)
+        it_w, c, _, wall_w = SG.run_warm(net, pr, E[-1], 2 * iters, T)
+        rows.append((it_p, wall_p, dice_p, it_w, wall_w, SG.run_warm.last_dice,
+                     SG.warm_start_dice(net, pr, T)))
+    a = np.array(rows, dtype=np.float64)
+    return {"grid": "32^3", "T": T, "train_pairs": 240, "mirror_images": 8, "epochs": 6,
+            "held_out": len(rows), "plain_iters": iters, "train_s": round(train_s, 1),
+            "plain_iters_to_energy": a[:, 0].astype(int).tolist(),
+            "warm_iters_to_energy": a[:, 3].astype(int).tolist(),
+            "plain_wall_ms_mean": round(1e3 * a[:, 1].mean(), 1),
+            "warm_wall_ms_mean": round(1e3 * a[:, 4].mean(), 1),
+            "wall_speedup": round(a[:, 1].sum() / a[:, 4].sum(), 3),
+            "warm_reached": int((a[:, 3] < 2 * iters).sum()),
+            "dice_plain": round(a[:, 2].mean(), 4), "dice_warm": round(a[:, 5].mean(), 4),
+            "dice_surrogate_only": round(a[:, 6].mean(), 4)}
+
+
 def ctypes_sizeof_energy():
     import ctypes
 
@@ -415,6 +454,8 @@ def main():
     ap.add_argument("--kmode", type=int, default=None, help="0 fp32, 1 bf16x3, 2 bf16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
+    ap.add_argument("--no-warm-start", action="store_true",
+                    help="skip the learned warm-start measurement (about a minute)")
     ap.add_argument("--grid", type=int, nargs=3, default=None, metavar=("X", "Y", "Z"),
                     help="override the 264 160 228 grid (tests only; the metric is quoted on the "
                          "default)")

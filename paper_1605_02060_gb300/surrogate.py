@@ -356,8 +356,50 @@ def run_warm(net, pair, target_energy, max_iters, T=10, k_mode=1):
             it += 1
             if e <= target_energy:
                 break
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        run_warm.last_dice = mask_dice(ctx, pair)
+    return it, c, nev, wall
+
+
+def run_plain_timed(pair, target_energy, max_iters, T=10, k_mode=1):
+    """Plain LDDMM from v = 0 until the energy reaches target_energy, timed like run_warm
+    (context creation included).  Returns (iterations, wall seconds, Dice of the transferred
+    template mask with the target mask)."""
+    n = pair.I0.shape
+    p = L.default_params(n[2], n[1], n[0], T=T, k_mode=k_mode)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     torch.cuda.synchronize()
-    return it, c, nev, time.perf_counter() - t0
+    t0 = time.perf_counter()
+    with L.Lddmm(p, dev(pair.I0), dev(pair.I1), dev(pair.M)) as ctx:
+        it, e = 0, float("inf")
+        while it < max_iters and e > target_energy:
+            e = ctx.step()["total"]
+            it += 1
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        d = mask_dice(ctx, pair)
+    return it, wall, d
+
+
+def mask_dice(ctx, pair):
+    """Dice of the template mask pulled back through the context's current map (nearest
+    neighbour, §2.5) with the target mask."""
+    L0 = (pair.I0 > 0.5).astype(np.uint16)
+    L1 = (pair.I1 > 0.5).astype(np.uint16)
+    return ctx.dice(ctx.transfer_labels(L0), L1)
+
+
+def warm_start_dice(net, pair, T=10, k_mode=1):
+    """Dice with the target mask of the template mask transferred by the surrogate's start alone
+    (smoothed and scaled by the energy, no LDDMM iteration)."""
+    n = pair.I0.shape
+    p = L.default_params(n[2], n[1], n[0], T=T, k_mode=k_mode)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    with L.Lddmm(p, dev(pair.I0), dev(pair.I1), dev(pair.M)) as ctx:
+        v = smooth_prediction(ctx, warm_start_field(net, pair, T), p.gamma)
+        choose_start(ctx, v)
+        return mask_dice(ctx, pair)
 
 
 def warm_start_field(net, pair, T=10):
