@@ -391,8 +391,10 @@ def measure_warm_start():
     a 4-level encoder-decoder (16/32/64/128 channels) trained on the GPU by the library's own
     kernels on 240 ellipsoid-union pairs (x8 mirror images) labelled by 60 plain iterations;
     on 8 held-out pairs the warm start (prediction smoothed by gamma^2 K, scaled by the energy)
-    iterates until it reaches the energy of 60 plain iterations.  Wall times include context
-    creation, prediction and the start's energy evaluations."""
+    iterates until it reaches the energy of 60 plain iterations.  Both use backtracking (a step
+    that raises the energy is undone, the step size halved): with a fixed step the plain energy
+    is not monotone.  Wall times include context creation, prediction, the start's energy
+    evaluations and undone steps."""
     import numpy as np
 
     from paper_1605_02060_gb300 import surrogate as SG
@@ -405,12 +407,19 @@ def measure_warm_start():
     train_s = time.perf_counter() - t0
     rows = []
     for pr in SG.make_pairs(8, n, seed0=5000, amp_max=4.0):
-        _, E, _, _ = SG.run_plain(pr, iters, T)
-        it_p, wall_p, dice_p = SG.run_plain_timed(pr, E[-1], 2 * iters, T)
-        it_w, c, _, wall_w = SG.run_warm(net, pr, E[-1], 2 * iters, T)
+        # both runs with backtracking, so that their energies never rise: the plain target is
+        # its energy after 60 accepted iterations
+        _, E, _, _ = SG.run_plain(pr, iters, T, flags=1)
+        it_p, wall_p, dice_p = SG.run_plain_timed(pr, E[-1], 2 * iters, T, flags=1)
+        it_w, c, _, wall_w = SG.run_warm(net, pr, E[-1], 2 * iters, T, flags=1)
+        # time to the plain method's Dice: the fewest warm iterations that match it (found
+        # untimed), then a timed run of exactly that many
+        kd = SG.warm_iters_to_dice(net, pr, dice_p, 2 * iters, T, flags=1)
+        wall_d = SG.run_warm_fixed(net, pr, kd, T, flags=1) if kd is not None else float("nan")
         rows.append((it_p, wall_p, dice_p, it_w, wall_w, SG.run_warm.last_dice,
-                     SG.warm_start_dice(net, pr, T)))
+                     SG.warm_start_dice(net, pr, T), -1 if kd is None else kd, wall_d))
     a = np.array(rows, dtype=np.float64)
+    okd = a[:, 7] >= 0
     return {"grid": "32^3", "T": T, "train_pairs": 240, "mirror_images": 8, "epochs": 6,
             "held_out": len(rows), "plain_iters": iters, "train_s": round(train_s, 1),
             "plain_iters_to_energy": a[:, 0].astype(int).tolist(),
@@ -418,9 +427,14 @@ def measure_warm_start():
             "plain_wall_ms_mean": round(1e3 * a[:, 1].mean(), 1),
             "warm_wall_ms_mean": round(1e3 * a[:, 4].mean(), 1),
             "wall_speedup": round(a[:, 1].sum() / a[:, 4].sum(), 3),
+            "wall_speedup_per_pair": [round(float(x), 2) for x in a[:, 1] / a[:, 4]],
+            "wall_speedup_median": round(float(np.median(a[:, 1] / a[:, 4])), 2),
             "warm_reached": int((a[:, 3] < 2 * iters).sum()),
             "dice_plain": round(a[:, 2].mean(), 4), "dice_warm": round(a[:, 5].mean(), 4),
-            "dice_surrogate_only": round(a[:, 6].mean(), 4)}
+            "dice_surrogate_only": round(a[:, 6].mean(), 4),
+            "warm_iters_to_plain_dice": a[:, 7].astype(int).tolist(),
+            "warm_to_dice_wall_ms_mean": round(1e3 * float(np.nanmean(a[okd, 8])), 1) if okd.any() else None,
+            "dice_wall_speedup": round(float(a[okd, 1].sum() / a[okd, 8].sum()), 3) if okd.all() else None}
 
 
 def ctypes_sizeof_energy():

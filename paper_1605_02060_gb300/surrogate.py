@@ -244,11 +244,12 @@ def make_pairs(count, n, seed0, amp_max=8.0):
     return pairs
 
 
-def run_plain(pair, iters, T=10, v0=None, target_energy=None, max_iters=None, k_mode=1):
+def run_plain(pair, iters, T=10, v0=None, target_energy=None, max_iters=None, k_mode=1, flags=0):
     """Plain LDDMM on one pair.  Returns (v, energies, iterations); with target_energy it stops
-    at the first iteration whose energy is <= target (at most max_iters)."""
+    at the first iteration whose energy is <= target (at most max_iters).  flags bit 0:
+    backtracking (a step that raises the energy is undone and the step size halved)."""
     n = pair.I0.shape
-    p = L.default_params(n[2], n[1], n[0], T=T, k_mode=k_mode)
+    p = L.default_params(n[2], n[1], n[0], T=T, k_mode=k_mode, flags=flags)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     with L.Lddmm(p, dev(pair.I0), dev(pair.I1), dev(pair.M)) as ctx:
         if v0 is not None:
@@ -339,11 +340,11 @@ def choose_start(ctx, v_pred, scales=(0.0, 0.5, 1.0, 1.5, 2.0, 3.0)):
     return best[0], best[1], len(scales)
 
 
-def run_warm(net, pair, target_energy, max_iters, T=10, k_mode=1):
+def run_warm(net, pair, target_energy, max_iters, T=10, k_mode=1, flags=0):
     """Warm start (choose_start on the prediction), then plain LDDMM until the energy reaches
     target_energy.  Returns (iterations, chosen scale, energy evaluations, wall seconds)."""
     n = pair.I0.shape
-    p = L.default_params(n[2], n[1], n[0], T=T, k_mode=k_mode)
+    p = L.default_params(n[2], n[1], n[0], T=T, k_mode=k_mode, flags=flags)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -362,12 +363,12 @@ def run_warm(net, pair, target_energy, max_iters, T=10, k_mode=1):
     return it, c, nev, wall
 
 
-def run_plain_timed(pair, target_energy, max_iters, T=10, k_mode=1):
+def run_plain_timed(pair, target_energy, max_iters, T=10, k_mode=1, flags=0):
     """Plain LDDMM from v = 0 until the energy reaches target_energy, timed like run_warm
     (context creation included).  Returns (iterations, wall seconds, Dice of the transferred
     template mask with the target mask)."""
     n = pair.I0.shape
-    p = L.default_params(n[2], n[1], n[0], T=T, k_mode=k_mode)
+    p = L.default_params(n[2], n[1], n[0], T=T, k_mode=k_mode, flags=flags)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -400,6 +401,40 @@ def warm_start_dice(net, pair, T=10, k_mode=1):
         v = smooth_prediction(ctx, warm_start_field(net, pair, T), p.gamma)
         choose_start(ctx, v)
         return mask_dice(ctx, pair)
+
+
+def warm_iters_to_dice(net, pair, dice_target, max_iters, T=10, k_mode=1, flags=0):
+    """Fewest warm-started iterations whose transferred template mask reaches Dice >=
+    dice_target with the target mask (0: the start itself), or None within max_iters."""
+    n = pair.I0.shape
+    p = L.default_params(n[2], n[1], n[0], T=T, k_mode=k_mode, flags=flags)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    with L.Lddmm(p, dev(pair.I0), dev(pair.I1), dev(pair.M)) as ctx:
+        v = smooth_prediction(ctx, warm_start_field(net, pair, T), p.gamma)
+        choose_start(ctx, v)
+        for it in range(max_iters + 1):
+            if mask_dice(ctx, pair) >= dice_target:
+                return it
+            if it < max_iters:
+                ctx.step()
+    return None
+
+
+def run_warm_fixed(net, pair, iters, T=10, k_mode=1, flags=0):
+    """Wall seconds of a warm start followed by exactly `iters` iterations (context creation,
+    prediction, smoothing and the start's energy evaluations included)."""
+    n = pair.I0.shape
+    p = L.default_params(n[2], n[1], n[0], T=T, k_mode=k_mode, flags=flags)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with L.Lddmm(p, dev(pair.I0), dev(pair.I1), dev(pair.M)) as ctx:
+        v = smooth_prediction(ctx, warm_start_field(net, pair, T), p.gamma)
+        choose_start(ctx, v)
+        for _ in range(iters):
+            ctx.step(want_energy=False)
+        torch.cuda.synchronize()
+    return time.perf_counter() - t0
 
 
 def warm_start_field(net, pair, T=10):

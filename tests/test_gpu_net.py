@@ -146,10 +146,12 @@ def test_trained_network_warm_start_saves_iterations(lib):
     assert hist[-1] < 0.5 * hist[0], hist
     warm, rels, cs = [], [], []
     for pr in SG.make_pairs(8, n, seed0=5000, amp_max=4.0):
-        v, E, _, _ = SG.run_plain(pr, iters, T)
+        v, _, _, _ = SG.run_plain(pr, iters, T)
         pred = SG.warm_start_field(net, pr, T)
         rels.append(_rel(pred, v.cpu().numpy()))
-        itw, c, nev, _ = SG.run_warm(net, pr, E[-1], 2 * iters, T)
+        # target and warm run with backtracking: their energies never rise
+        _, E, _, _ = SG.run_plain(pr, iters, T, flags=1)
+        itw, c, nev, _ = SG.run_warm(net, pr, E[-1], 2 * iters, T, flags=1)
         warm.append(itw)
         cs.append(c)
     print("\nheld-out prediction rel-L2 %s; chosen scales %s; warm iterations to the plain energy "
