@@ -306,37 +306,55 @@ void launch_fwd_terms(const Grid& g, const float* u_cur, const void* I0, const f
                                                ihz);
 }
 
-// Forward sweep, flow: u_next = -dt v_j/h + u_cur(x - dt v_j/h); at the last step J0_T and
-// E_data.
-template <typename ST>
-__global__ void k_fwd_flow(Grid g, const ST* __restrict__ vj, const float* __restrict__ uc,
-                           float* __restrict__ un, float dtx, float dty, float dtz, int last,
-                           const ST* __restrict__ I0, const ST* __restrict__ I1,
-                           const ST* __restrict__ M, float* __restrict__ J0T, Acc* acc) {
-  int x, y, z, idx;
-  const bool in = voxel3d(g, x, y, z, idx);
+// Forward sweep, last step: u_T = -dt v_{T-1}/h + u_cur(x - dt v_{T-1}/h), then J0_T = I0 o
+// (id + u_T) and E_data = sum M (J0_T - I1)^2.  Marches ZC planes per thread like k_disp_march
+// (the velocity of plane z+1 is loaded before plane z's lookups), so the three dependent
+// latencies of a voxel (v, the map at the displaced point, I0 at the mapped point) overlap with
+// the next plane's.
+template <typename ST, int ZC>
+__global__ void __launch_bounds__(256) k_fwd_last_march(Grid g, const ST* __restrict__ vj,
+                                                        const float* __restrict__ uc,
+                                                        float* __restrict__ un, float dtx,
+                                                        float dty, float dtz,
+                                                        const ST* __restrict__ I0,
+                                                        const ST* __restrict__ I1,
+                                                        const ST* __restrict__ M,
+                                                        float* __restrict__ J0T, Acc* acc) {
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
   float edata = 0.f;
-  if (in) {
-    const float v0 = ldf(vj + idx), v1 = ldf(vj + g.N + idx), v2 = ldf(vj + 2 * g.N + idx);
-    const float dx = dtx * v0, dy = dty * v1, dz = dtz * v2;
-    float ox = -dx, oy = -dy, oz = -dz;
-    if (uc) {
-      Tri w = tri_setup(g, (float)x - dx, (float)y - dy, (float)z - dz);
-      ox += tri_apply(uc, w);
-      oy += tri_apply(uc + g.N, w);
-      oz += tri_apply(uc + 2 * g.N, w);
-    }
-    un[idx] = ox;
-    un[g.N + idx] = oy;
-    un[2 * g.N + idx] = oz;
-    if (last) {
+  if (x < g.nx && y < g.ny) {
+    const int z0 = blockIdx.z * ZC, z1 = min(z0 + ZC, g.nz);
+    const int plane = g.nx * g.ny;
+    int idx = (z0 * g.ny + y) * g.nx + x;
+    float a0 = ldf(vj + idx), a1 = ldf(vj + g.N + idx), a2 = ldf(vj + 2 * g.N + idx);
+    for (int z = z0; z < z1; ++z, idx += plane) {
+      float n0 = 0.f, n1 = 0.f, n2 = 0.f;
+      if (z + 1 < z1) {
+        n0 = ldf_now(vj + idx + plane);
+        n1 = ldf_now(vj + g.N + idx + plane);
+        n2 = ldf_now(vj + 2 * g.N + idx + plane);
+      }
+      const float dx = dtx * a0, dy = dty * a1, dz = dtz * a2;
+      float ox = -dx, oy = -dy, oz = -dz;
+      if (uc) {
+        const Tri w = tri_setup(g, (float)x - dx, (float)y - dy, (float)z - dz);
+        ox += tri_apply(uc, w);
+        oy += tri_apply(uc + g.N, w);
+        oz += tri_apply(uc + 2 * g.N, w);
+      }
+      un[idx] = ox;
+      un[g.N + idx] = oy;
+      un[2 * g.N + idx] = oz;
       const float j0 = tri_apply_t(I0, tri_setup(g, (float)x + ox, (float)y + oy, (float)z + oz));
       J0T[idx] = j0;
       const float r = j0 - ldf(I1 + idx);
-      edata = ldf(M + idx) * r * r;
+      edata = fmaf(ldf(M + idx) * r, r, edata);
+      a0 = n0;
+      a1 = n1;
+      a2 = n2;
     }
   }
-  if (last) block_sum_f_atomic(edata, &acc->e_data);
+  block_sum_f_atomic(edata, &acc->e_data);
 }
 
 void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u_next,
@@ -346,14 +364,15 @@ void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u
     disp_step(-1, g, vj, u_cur, u_next, dtx, dty, dtz, s, st);
     return;
   }
+  const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + kFlowZ - 1) / kFlowZ);
   if (st)
-    k_fwd_flow<<<grid3d(g), kBlock3d, 0, s>>>(
-        g, (const __nv_bfloat16*)vj, u_cur, u_next, dtx, dty, dtz, last ? 1 : 0,
-        (const __nv_bfloat16*)I0, (const __nv_bfloat16*)I1, (const __nv_bfloat16*)M, J0T, acc);
+    k_fwd_last_march<__nv_bfloat16, kFlowZ><<<grid, kBlock3d, 0, s>>>(
+        g, (const __nv_bfloat16*)vj, u_cur, u_next, dtx, dty, dtz, (const __nv_bfloat16*)I0,
+        (const __nv_bfloat16*)I1, (const __nv_bfloat16*)M, J0T, acc);
   else
-    k_fwd_flow<<<grid3d(g), kBlock3d, 0, s>>>(g, (const float*)vj, u_cur, u_next, dtx, dty, dtz,
-                                              last ? 1 : 0, (const float*)I0, (const float*)I1,
-                                              (const float*)M, J0T, acc);
+    k_fwd_last_march<float, kFlowZ><<<grid, kBlock3d, 0, s>>>(
+        g, (const float*)vj, u_cur, u_next, dtx, dty, dtz, (const float*)I0, (const float*)I1,
+        (const float*)M, J0T, acc);
 }
 
 // --------------------------------------------------------------------------------------------
