@@ -1,5 +1,6 @@
 // Host-side launch wrappers for the liblddmm kernels (one translation unit per kernel family).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -43,9 +44,11 @@ void launch_flow_back(const Grid& g, const void* vj, const float* u_next, float*
 void launch_interleave(const void* a, const void* b, void* out, int64_t n, cudaStream_t s,
                        int st);
 // Forward sweep step j: b = c W_j (J0_j - J1_j) grad J0_j / h,  J0_j = I0 o (id + u_cur).
+// bsplit 0: b as 3 fp32 fields; 1 / 2: b split for the pre-split K (bf16 hi plane / hi and lo
+// planes, rows of pitch px).
 void launch_fwd_terms(const Grid& g, const float* u_cur, const void* I0, const float* J1j,
                       const float* Wj, float* b, float c, float ihx, float ihy, float ihz,
-                      cudaStream_t s, int st);
+                      cudaStream_t s, int st, int bsplit = 0, int px = 0);
 // Forward sweep step j: u_next = -dt v_j / h + u_cur(x - dt v_j / h) (u_cur == nullptr: id);
 // if last, J0_T = I0 o (id + u_next) and E_data.
 void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u_next,
@@ -101,6 +104,12 @@ struct KPlan {
   uint16_t* tcx[2];
   float* xtail[2];
   int xtw;
+  // operand tables of the pre-split pass (kernels_ks.cu) per axis and direction: bf16
+  // [2][Nc][Kp] (hi plane, lo plane), row n = output column (Nc = min(256, ceil16(n))), k
+  // contiguous (Kp = ceil16(n)), zero beyond the axis length; for 256 < nx <= 264 the x
+  // columns 256.. as float [ceil64(nx)][8] (kstail, zero padded)
+  uint16_t* ks[3][2];
+  float* kstail[2];
   int* err;  // device flag set by a tensor-core kernel whose bounded wait timed out
 };
 // Build device tables for one grid (allocates; free with kplan_destroy).
@@ -111,13 +120,43 @@ void kplan_destroy(KPlan* kp);
 // ncomp*N floats.  in and out may alias.  mode: LDDMM_K_*.
 // If v_upd != nullptr the result is not stored: instead v_upd <- v_upd - eps (2 v_upd - K in)
 // (the gradient-descent update, fused into the last pass on the tensor-core path).
+// cap: floats available in out and in work (0: ncomp*N); the tensor-core modes take the
+// pre-split path when cap >= ks_field_floats (intermediate fields with padded rows).
 cudaError_t apply_K(const KPlan& kp, int mode, const float* in, float* out, float* work,
                     int ncomp, cudaStream_t s, const Hook& hook = Hook(),
-                    float* v_upd = nullptr, float eps = 0.f);
+                    float* v_upd = nullptr, float eps = 0.f, long long cap = 0,
+                    bool in_split = false);
 // Persistent warp-specialised TMA/tcgen05 pass (kernels_tma.cu) and its shape condition.
 bool tma_pass_supported(const KPlan& kp, int axis);
 cudaError_t tma_axis_pass(const KPlan& kp, int axis, bool inverse, int split, const float* in,
                           float* out, int ncomp, int epi, float eps, cudaStream_t s);
+// Output addressing of a pre-split pass: line l = (a D + b) E + e is written at column n to
+// element (a F + b) P + e + n G, as bf16 hi/lo planes `plane` elements apart (KS_OUT_SPLIT), as
+// fp32 (KS_OUT_F32), or as the update out <- out - eps (2 out - C) of fp32 rows (KS_OUT_UPD);
+// sym: scale by the K symbol of the z-forward product.
+enum { KS_OUT_SPLIT = 0, KS_OUT_F32 = 1, KS_OUT_UPD = 2 };
+struct KsOut {
+  int kind;
+  int sym;
+  void* out;
+  long long plane;
+  long long D, E, F, P, G;
+};
+// cuTensorMapEncodeTiled from the driver, as void* (nullptr when unavailable).
+void* tma_encode_fn();
+// The pre-split path (all six products on k_dft_ks).  Row pitch of a split line (elements),
+// support test, and the floats a buffer needs for any intermediate field of ncomp components.
+int ks_pitch(int L);
+bool ks_supported(const KPlan& kp);
+long long ks_field_floats(int nx, int ny, int nz, int ncomp);
+cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, const void* in,
+                         long long nlines, const KsOut& o, float eps, cudaStream_t s);
+// True when apply_K(kp, mode, ..., ncomp, cap) takes the pre-split path; its input may then be
+// given already split (in_split): bf16 hi/lo planes [ncomp][nz][ny][ks_pitch(nx)].
+bool ks_path(const KPlan& kp, int mode, int ncomp, long long cap);
+// fp32 rows [nrows][L] -> split field at the addresses `o` gives (line = row, column = n).
+cudaError_t ks_split_rows(const float* in, long long nrows, int L, int split, const KsOut& o,
+                          cudaStream_t s);
 // One tensor-core axis pass (kernels_tc.cu): epi 0 plain, 1 times the K symbol, 2 update.
 cudaError_t tc_axis_pass(const KPlan& kp, int axis, bool inverse, int split, const float* in,
                          float* out, int ncomp, int epi, float eps, cudaStream_t s);

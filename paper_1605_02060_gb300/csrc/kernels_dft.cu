@@ -83,6 +83,33 @@ static void tc_table(const std::vector<float>& R, int n, bool inverse, int rows,
   }
 }
 
+// Operand table of the pre-split pass: B(k, n) as bf16 [hi plane][lo plane], each [Nc][Kp]
+// row-major (row n = output column, k contiguous), Nc = min(256, ceil16(n)), Kp = ceil16(n),
+// zero for n >= n_len or k >= n_len.
+static void ks_table(const std::vector<float>& R, int n, bool inverse, std::vector<uint16_t>& t) {
+  const int Kp = (n + 15) / 16 * 16, Nc = Kp < 256 ? Kp : 256;
+  const size_t plane = (size_t)Nc * Kp;
+  t.assign(2 * plane, 0);
+  for (int row = 0; row < n && row < Nc; ++row)
+    for (int k = 0; k < n; ++k) {
+      const float b = inverse ? R[(size_t)k * n + row] : R[(size_t)row * n + k];
+      const uint16_t bh = bf16_rn(b);
+      t[(size_t)row * Kp + k] = bh;
+      t[plane + (size_t)row * Kp + k] = bf16_rn(b - bf16_to_f(bh));
+    }
+}
+
+// Columns 256..n-1 (at most 8) of B for the pre-split x pass, float [ceil64(n)][8].
+static void ks_tail_table(const std::vector<float>& R, int n, bool inverse, std::vector<float>& t) {
+  const int rows = (n + 63) / 64 * 64;
+  t.assign((size_t)rows * 8, 0.f);
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < 8 && 256 + j < n; ++j) {
+      const int col = 256 + j;
+      t[(size_t)k * 8 + j] = inverse ? R[(size_t)k * n + col] : R[(size_t)col * n + k];
+    }
+}
+
 // FP32 tail columns 256..n-1 of B as [Kpad][8] (zero beyond n and for j >= n - 256).
 static void tail_table(const std::vector<float>& R, int n, bool inverse, std::vector<float>& t) {
   const int Kpad = (n + 15) / 16 * 16;
@@ -121,6 +148,18 @@ cudaError_t kplan_create(KPlan* kp, int nx, int ny, int nz, float hx, float hy, 
       tc_table(R, n[d], dir == 1, (n[d] + 15) / 16 * 16, t);
       if ((e = upload(&kp->tc[d][dir], t)) != cudaSuccess) return e;
     }
+    if (n[d] <= (d == 0 ? 264 : 256)) {
+      for (int dir = 0; dir < 2; ++dir) {
+        std::vector<uint16_t> t;
+        ks_table(R, n[d], dir == 1, t);
+        if ((e = upload(&kp->ks[d][dir], t)) != cudaSuccess) return e;
+        if (d == 0 && n[d] > 256) {
+          std::vector<float> tt;
+          ks_tail_table(R, n[d], dir == 1, tt);
+          if ((e = upload(&kp->kstail[dir], tt)) != cudaSuccess) return e;
+        }
+      }
+    }
     if (d == 0 && nx > 256 && nx <= 264) {
       kp->xtw = nx - 256;
       for (int dir = 0; dir < 2; ++dir) {
@@ -148,6 +187,9 @@ void kplan_destroy(KPlan* kp) {
   for (int dir = 0; dir < 2; ++dir) {
     if (kp->tcx[dir]) cudaFree(kp->tcx[dir]);
     if (kp->xtail[dir]) cudaFree(kp->xtail[dir]);
+    for (int d = 0; d < 3; ++d)
+      if (kp->ks[d][dir]) cudaFree(kp->ks[d][dir]);
+    if (kp->kstail[dir]) cudaFree(kp->kstail[dir]);
   }
   *kp = KPlan{};
 }
@@ -292,9 +334,76 @@ static cudaError_t apply_K_fp32(const KPlan& kp, const float* in, float* out, fl
   return cudaGetLastError();
 }
 
+// Tensor-core K over pre-split intermediate fields.  Every pass reads its input with the
+// transformed axis contiguous and writes its output in the next pass's line order:
+//   x fwd:  [c][z][y][x]  (split, x rows, pitch Px)  -> [c][x'][z][y]  (split, y rows, pitch Py)
+//   y fwd:                                            -> [c][x'][y'][z] (split, z rows, pitch Pz)
+//   z fwd + symbol:                                   -> [c][x'][y'][z'] (split, same order)
+//   z inv:                                            -> [c][z][x'][y'] (split, y rows, pitch Py)
+//   y inv:                                            -> [c][z][y][x']  (split, x rows, pitch Px)
+//   x inv:                                            -> fp32 [c][z][y][x], or the update of v
+// The buffers alternate between work and out (in may alias out).  A plain fp32 input is first
+// split into work; without the update the result then lands in work and is copied to out.
+static cudaError_t apply_K_ks(const KPlan& kp, int split, const float* in, float* out,
+                              float* work, int ncomp, cudaStream_t s, const Hook& hook,
+                              float* v_upd, float eps, bool in_split) {
+  const long long X = kp.nx, Y = kp.ny, Z = kp.nz, C = ncomp;
+  const long long Px = ks_pitch(kp.nx), Py = ks_pitch(kp.ny), Pz = ks_pitch(kp.nz);
+  cudaError_t e;
+  float* bA = work;   // receives the x forward product
+  float* bB = out;
+  const void* src = in;
+  if (!in_split) {
+    const KsOut o0{KS_OUT_SPLIT, 0, work, C * Z * Y * Px, 1, 1, 1, Px, 1};
+    if ((e = ks_split_rows(in, C * Z * Y, kp.nx, split, o0, s)) != cudaSuccess) return e;
+    src = work;
+    bA = out;
+    bB = work;
+  }
+  struct Pass {
+    int kid, axis;
+    bool inv;
+    long long nlines;
+    KsOut o;
+  };
+  const Pass ps[5] = {
+      {KID_KX_FWD, 0, false, C * Z * Y, {KS_OUT_SPLIT, 0, bA, C * X * Z * Py, Z, Y, X * Z, Py, Z * Py}},
+      {KID_KY_FWD, 1, false, C * X * Z, {KS_OUT_SPLIT, 0, bB, C * X * Y * Pz, 1, Z, Y, Pz, Pz}},
+      {KID_KZ_SYM, 2, false, C * X * Y, {KS_OUT_SPLIT, 1, bA, C * X * Y * Pz, 1, 1, 1, Pz, 1}},
+      {KID_KZ_INV, 2, true, C * X * Y, {KS_OUT_SPLIT, 0, bB, C * Z * X * Py, X, Y, Z * X, Py, X * Py}},
+      {KID_KY_INV, 1, true, C * Z * X, {KS_OUT_SPLIT, 0, bA, C * Z * Y * Px, 1, X, Y, Px, Px}}};
+  for (int p = 0; p < 5; ++p) {
+    hook(ps[p].kid, 0);
+    e = ks_axis_pass(kp, ps[p].axis, ps[p].inv, split, src, ps[p].nlines, ps[p].o, 0.f, s);
+    hook(ps[p].kid, 1);
+    if (e != cudaSuccess) return e;
+    src = ps[p].o.out;
+  }
+  // x inverse: from bA into v_upd (update) or fp32 rows
+  float* dst = v_upd ? v_upd : bB;
+  const KsOut o6{v_upd ? KS_OUT_UPD : KS_OUT_F32, 0, dst, 0, 1, 1, 1, X, 1};
+  hook(KID_KX_INV, 0);
+  e = ks_axis_pass(kp, 0, true, split, src, C * Z * Y, o6, eps, s);
+  hook(KID_KX_INV, 1);
+  if (e != cudaSuccess) return e;
+  if (!v_upd && dst != out)
+    e = cudaMemcpyAsync(out, dst, (size_t)C * X * Y * Z * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  return e;
+}
+
+bool ks_path(const KPlan& kp, int mode, int ncomp, long long cap) {
+  if (mode != LDDMM_K_BF16X3 && mode != LDDMM_K_BF16) return false;
+  const long long N = (long long)kp.nx * kp.ny * kp.nz;
+  if (cap <= 0) cap = (long long)ncomp * N;
+  return ks_supported(kp) && cap >= ks_field_floats(kp.nx, kp.ny, kp.nz, ncomp);
+}
+
 static cudaError_t apply_K_tc(const KPlan& kp, int split, const float* in, float* out,
                               float* work, int ncomp, cudaStream_t s, const Hook& hook,
-                              float* v_upd, float eps) {
+                              float* v_upd, float eps, long long cap, bool in_split) {
+  if (ks_path(kp, split ? LDDMM_K_BF16X3 : LDDMM_K_BF16, ncomp, cap))
+    return apply_K_ks(kp, split, in, out, work, ncomp, s, hook, v_upd, eps, in_split);
+  if (in_split) return cudaErrorInvalidValue;
   cudaError_t e;
 #define TC_PASS(kid, axis, inv, src, dst, epi)                                         \
   do {                                                                                 \
@@ -317,9 +426,11 @@ static cudaError_t apply_K_tc(const KPlan& kp, int split, const float* in, float
 }
 
 cudaError_t apply_K(const KPlan& kp, int mode, const float* in, float* out, float* work,
-                    int ncomp, cudaStream_t s, const Hook& hook, float* v_upd, float eps) {
+                    int ncomp, cudaStream_t s, const Hook& hook, float* v_upd, float eps,
+                    long long cap, bool in_split) {
   switch (mode) {
     case LDDMM_K_FP32: {
+      if (in_split) return cudaErrorInvalidValue;
       cudaError_t e = apply_K_fp32(kp, in, out, work, ncomp, s, hook);
       if (e != cudaSuccess || !v_upd) return e;
       Grid g{kp.nx, kp.ny, kp.nz, kp.nx * kp.ny * kp.nz};
@@ -329,9 +440,9 @@ cudaError_t apply_K(const KPlan& kp, int mode, const float* in, float* out, floa
       return cudaGetLastError();
     }
     case LDDMM_K_BF16X3:
-      return apply_K_tc(kp, 1, in, out, work, ncomp, s, hook, v_upd, eps);
+      return apply_K_tc(kp, 1, in, out, work, ncomp, s, hook, v_upd, eps, cap, in_split);
     case LDDMM_K_BF16:
-      return apply_K_tc(kp, 0, in, out, work, ncomp, s, hook, v_upd, eps);
+      return apply_K_tc(kp, 0, in, out, work, ncomp, s, hook, v_upd, eps, cap, in_split);
     default:
       return cudaErrorNotSupported;
   }

@@ -248,10 +248,16 @@ __device__ __forceinline__ float J0_at(const Grid& g, const float* __restrict__ 
                                    (float)z + __ldg(u + 2 * g.N + idx)));
 }
 
-template <typename ST>
-__global__ void k_fwd_terms(Grid g, const float* __restrict__ uc, const ST* __restrict__ I0,
-                            const float* __restrict__ J1j, const float* __restrict__ Wj,
-                            float* __restrict__ b, float c, float ihx, float ihy, float ihz) {
+// b as fp32 components (bsplit == 0), or split into bf16 hi/lo planes for the pre-split K
+// (bsplit 1: hi plane only, 2: hi and lo): element ((comp Z + z) Y + y) px + x of each plane,
+// planes 3 Z Y px elements apart.
+template <typename ST, int BSPLIT>
+__global__ void __launch_bounds__(256, 8) k_fwd_terms(Grid g, const float* __restrict__ uc,
+                                                      const ST* __restrict__ I0,
+                                                      const float* __restrict__ J1j,
+                                                      const float* __restrict__ Wj,
+                                                      float* __restrict__ b, float c, float ihx,
+                                                      float ihy, float ihz, int px) {
   int x, y, z, idx;
   if (!voxel3d(g, x, y, z, idx)) return;
   const float w = Wj[idx];
@@ -290,20 +296,40 @@ __global__ void k_fwd_terms(Grid g, const float* __restrict__ uc, const ST* __re
       bz = r * gr[2] * ihz;
     }
   }
-  b[idx] = bx;
-  b[g.N + idx] = by;
-  b[2 * g.N + idx] = bz;
+  if (BSPLIT) {
+    __nv_bfloat16* h = reinterpret_cast<__nv_bfloat16*>(b);
+    const int64_t cs = (int64_t)g.nz * g.ny * px;
+    const int64_t o = ((int64_t)z * g.ny + y) * px + x;
+    const float bc[3] = {bx, by, bz};
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const __nv_bfloat16 hb = __float2bfloat16_rn(bc[e]);
+      h[e * cs + o] = hb;
+      if (BSPLIT == 2) h[3 * cs + e * cs + o] = __float2bfloat16_rn(bc[e] - __bfloat162float(hb));
+    }
+  } else {
+    b[idx] = bx;
+    b[g.N + idx] = by;
+    b[2 * g.N + idx] = bz;
+  }
 }
 
 void launch_fwd_terms(const Grid& g, const float* u_cur, const void* I0, const float* J1j,
                       const float* Wj, float* b, float c, float ihx, float ihy, float ihz,
-                      cudaStream_t s, int st) {
-  if (st)
-    k_fwd_terms<<<grid3d(g), kBlock3d, 0, s>>>(g, u_cur, (const __nv_bfloat16*)I0, J1j, Wj, b, c,
-                                               ihx, ihy, ihz);
-  else
-    k_fwd_terms<<<grid3d(g), kBlock3d, 0, s>>>(g, u_cur, (const float*)I0, J1j, Wj, b, c, ihx, ihy,
-                                               ihz);
+                      cudaStream_t s, int st, int bsplit, int px) {
+#define FWD_TERMS(ST_, BS_)                                                                    \
+  k_fwd_terms<ST_, BS_><<<grid3d(g), kBlock3d, 0, s>>>(g, u_cur, (const ST_*)I0, J1j, Wj, b, c, \
+                                                       ihx, ihy, ihz, px)
+  if (st) {
+    if (bsplit == 2) FWD_TERMS(__nv_bfloat16, 2);
+    else if (bsplit == 1) FWD_TERMS(__nv_bfloat16, 1);
+    else FWD_TERMS(__nv_bfloat16, 0);
+  } else {
+    if (bsplit == 2) FWD_TERMS(float, 2);
+    else if (bsplit == 1) FWD_TERMS(float, 1);
+    else FWD_TERMS(float, 0);
+  }
+#undef FWD_TERMS
 }
 
 // Forward sweep, last step: u_T = -dt v_{T-1}/h + u_cur(x - dt v_{T-1}/h), then J0_T = I0 o

@@ -1,0 +1,587 @@
+// Tensor-core axis pass over a pre-split field, for all six products of K (§2.4):
+//     C(l, n) = sum_k A(l, k) B(k, n)       over all lines l of one axis,
+// with B = R or R^T (the orthonormal real DFT basis of that axis).
+//
+// The field arrives already split into bf16 hi and lo planes (A = hi + lo to 16 mantissa bits),
+// laid out [line][k] with the transformed axis contiguous (K-major).  A TMA load of a 64 k x
+// 128 line box with the 128-byte swizzle therefore lands directly in the canonical swizzled
+// operand layout of tcgen05.mma: there is no conversion step between the copy and the tensor
+// cores.  The previous pass wrote the field that way: its epilogue stores its output transposed
+// into the next axis's line order, split into hi and lo, so the only per-element work left is
+// in the epilogues.  The split costs no extra bytes (2 x 2 bytes per fp32 value).
+//
+// Roles inside one CTA (one persistent CTA per SM, 448 threads):
+//   warp 0      TMA producer: A hi/lo boxes into an AS-deep ring; B (bf16 hi/lo tables of the
+//               axis, [Nc][Kp]) either resident (loaded once) or streamed per 64-k block;
+//   warp 1      TMEM owner and MMA issuer (one thread): hi*hi + hi*lo + lo*hi per 16-k step into
+//               a double-buffered TMEM accumulator (2 x Nc <= 512 columns);
+//   warps 2-9   epilogue: tcgen05.ld of 16/32 columns (warp w reads TMEM lanes 32(w%4)..+31, the
+//               two warps of a lane quadrant split the columns), optional K symbol or the
+//               gradient-descent update, stores;
+//   warps 10-13 x axis longer than 256 only: the output columns 256.. in FP32 on the CUDA cores,
+//               one line per thread, read from the same A stages (hi + lo) as the MMA; an A
+//               stage is free once the MMA has committed and these 128 threads have arrived.
+// Every wait is bounded and observes a CTA-wide abort flag; on abort the kernel drains its
+// copies and MMAs, frees TMEM and reports through *err.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "kernels.h"
+#include "tc_ptx.cuh"
+
+namespace lddmm {
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+constexpr int KS_NT = 448;
+constexpr int KS_W_TMA = 0, KS_W_MMA = 1, KS_W_TAIL = 10;
+constexpr int KS_NEPI = 8;                 // epilogue warps 2..9
+constexpr int KS_NTAIL = 128;              // tail threads (warps 10..13)
+constexpr int KS_ABOX = 128 * 128;         // one A box: 128 lines x 64 bf16 (16 KB)
+constexpr int KS_MAXS = 6;                 // ring depths (A and streamed B) at most
+
+struct KsArgs {
+  int nlines;          // lines of the input field
+  int L;               // transform length: valid k and valid output columns
+  int Nc;              // output columns on the tensor cores (L rounded up to 16, at most 256)
+  int nk, nkb;         // 16-wide k-steps and 64-wide k-blocks over the whole length
+  int split;           // 1: three products (hi*hi + hi*lo + lo*hi), 0: hi*hi
+  int AS, BS, bres;    // A ring depth; streamed B ring depth; 1: B resident (nkb blocks)
+  int ntiles;          // 128-line tiles
+  int tw;              // FP32 tail columns 256..256+tw-1 (x axis longer than 256), else 0
+  const float* tail;   // their table B(k, 256 + j) as float [nkb * 64][8], zero padded
+  KsOut o;             // output addressing
+  float eps;           // KS_OUT_UPD: step size
+  int stage;           // 1: row-wise output (o.G == 1), staged through shared memory
+  const float* lx;     // symbol (o.sym): lambda per x, y, z frequency
+  const float* ly;
+  const float* lz;
+  float alpha, gamma;
+  int X, Y;            // symbol: line l = (c X + x) Y + y
+  int* err;
+};
+
+__host__ __device__ inline int ks_abytes(int split) { return (split ? 2 : 1) * KS_ABOX; }
+__host__ __device__ inline int ks_bbytes(int split, int Nc) { return (split ? 2 : 1) * Nc * 128; }
+__host__ __device__ inline int ks_tbytes(const KsArgs& a) { return a.tw ? a.nkb * 64 * 8 * 4 : 0; }
+// per epilogue warp: 32 lines x 16 columns of fp32, rows padded to 17 (conflict-free transpose)
+constexpr int KS_SROW = 17;
+__host__ __device__ inline int ks_sbytes(const KsArgs& a) {
+  return a.stage ? KS_NEPI * 32 * KS_SROW * 4 : 0;
+}
+__host__ __device__ inline int ks_smem(const KsArgs& a) {
+  return 1024 + a.AS * ks_abytes(a.split) + (a.bres ? a.nkb : a.BS) * ks_bbytes(a.split, a.Nc) +
+         ks_tbytes(a) + ks_sbytes(a);
+}
+
+// tcgen05 shared-memory descriptor for a K-major operand in the 128-byte swizzled layout:
+// rows of 128 bytes (64 bf16 of k), 8-row atoms of 1024 bytes (SBO), atoms 1024-byte aligned;
+// a 16-k step inside the 128-byte row advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;                    // LBO (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;          // SBO: 8 rows x 128 bytes
+  d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                    // layout: 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(__nv_bfloat16 b) {
+  return *reinterpret_cast<const uint16_t*>(&b);
+}
+
+// hi = bf16(x), lo = bf16(x - hi): x = hi + lo to 16 mantissa bits.
+__device__ __forceinline__ void split1(float x, uint16_t& h, uint16_t& l) {
+  const __nv_bfloat16 hb = __float2bfloat16_rn(x);
+  h = bf16_bits(hb);
+  l = bf16_bits(__float2bfloat16_rn(x - __bfloat162float(hb)));
+}
+
+// 8 bf16 (one 16-byte word, element 0 in the low half of the first word) added to x[0..7]
+__device__ __forceinline__ void add_bf8(uint4 w, float* x) {
+  const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    x[2 * j] += __uint_as_float(u[j] << 16);
+    x[2 * j + 1] += __uint_as_float(u[j] & 0xffff0000u);
+  }
+}
+
+// Element offset of (line l, column 0): l = (a D + b) E + e -> (a F + b) P + e.
+__device__ __forceinline__ long long out_base(const KsOut& o, long long l) {
+  const long long e = l % o.E, t = l / o.E;
+  return (t / o.D * o.F + t % o.D) * o.P + e;
+}
+
+// Store cnt consecutive output columns n0.. of one line, one element at a time (transposed
+// outputs and the FP32 tail columns).
+__device__ __forceinline__ void store_scalar(const KsOut& o, int split, float eps, long long base,
+                                             int n0, const float* vc, int cnt) {
+  if (o.kind == KS_OUT_SPLIT) {
+    uint16_t* oh = reinterpret_cast<uint16_t*>(o.out);
+    for (int j = 0; j < cnt; ++j) {
+      uint16_t h, lo;
+      split1(vc[j], h, lo);
+      const long long off = base + (long long)(n0 + j) * o.G;
+      oh[off] = h;
+      if (split) oh[o.plane + off] = lo;
+    }
+  } else {
+    float* of = reinterpret_cast<float*>(o.out);
+    for (int j = 0; j < cnt; ++j) {
+      const long long off = base + (long long)(n0 + j) * o.G;
+      if (o.kind == KS_OUT_UPD) {
+        const float w = of[off];
+        of[off] = w - eps * (2.f * w - vc[j]);
+      } else {
+        of[off] = vc[j];
+      }
+    }
+  }
+}
+
+// Row-wise output of 16 columns n0.. for the 32 lines line0.. of one warp (lane = line on
+// entry): the values go through the warp's shared-memory tile so that each store instruction
+// writes two 16-column segments of two rows (rows of o.P elements, line l at l * o.P).
+__device__ __forceinline__ void store_rows_staged(const KsOut& o, int split, float eps,
+                                                  float* sg, int lane, long long line0,
+                                                  long long nlines, int n0, int ncols,
+                                                  const float* vc) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) sg[lane * KS_SROW + j] = vc[j];
+  __syncwarp();
+  const int jj = lane & 15, rh = lane >> 4;
+  const int n = n0 + jj;
+  if (o.kind == KS_OUT_UPD) {
+    float* of = reinterpret_cast<float*>(o.out);
+    float old[16];
+#pragma unroll
+    for (int it = 0; it < 16; ++it) {
+      const long long l = line0 + 2 * it + rh;
+      old[it] = (l < nlines && n < ncols) ? of[l * o.P + n] : 0.f;
+    }
+#pragma unroll
+    for (int it = 0; it < 16; ++it) {
+      const int r = 2 * it + rh;
+      const long long l = line0 + r;
+      if (l < nlines && n < ncols)
+        of[l * o.P + n] = old[it] - eps * (2.f * old[it] - sg[r * KS_SROW + jj]);
+    }
+  } else if (o.kind == KS_OUT_F32) {
+    float* of = reinterpret_cast<float*>(o.out);
+#pragma unroll
+    for (int it = 0; it < 16; ++it) {
+      const int r = 2 * it + rh;
+      const long long l = line0 + r;
+      if (l < nlines && n < ncols) of[l * o.P + n] = sg[r * KS_SROW + jj];
+    }
+  } else {
+    uint16_t* oh = reinterpret_cast<uint16_t*>(o.out);
+#pragma unroll
+    for (int it = 0; it < 16; ++it) {
+      const int r = 2 * it + rh;
+      const long long l = line0 + r;
+      if (l < nlines && n < ncols) {
+        uint16_t h, lo;
+        split1(sg[r * KS_SROW + jj], h, lo);
+        oh[l * o.P + n] = h;
+        if (split) oh[o.plane + l * o.P + n] = lo;
+      }
+    }
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUtensorMap tmA,
+                                                     const __grid_constant__ CUtensorMap tmB,
+                                                     KsArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem_dyn[];
+  __shared__ __align__(8) uint64_t b_afull[KS_MAXS], b_aempty[KS_MAXS], b_bfull[KS_MAXS],
+      b_bempty[KS_MAXS];
+  __shared__ __align__(8) uint64_t b_tfull[2], b_tempty[2], b_fin;
+  __shared__ uint32_t tmem_sh;
+  __shared__ int abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* smem = smem_dyn + ((1024u - (ptx::smem_u32(smem_dyn) & 1023u)) & 1023u);
+  const int abytes = ks_abytes(a.split), bbytes = ks_bbytes(a.split, a.Nc);
+  uint8_t* aring = smem;
+  uint8_t* bring = smem + a.AS * abytes;
+  float* ttab = reinterpret_cast<float*>(bring + (a.bres ? a.nkb : a.BS) * bbytes);
+  float* stg = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(ttab) + ks_tbytes(a));
+  volatile int* abort = &abort_sh;
+
+  if (warp == KS_W_MMA) {
+    ptx::tmem_alloc(ptx::smem_u32(&tmem_sh), 512u);
+    ptx::tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < a.AS; ++i) {
+      ptx::mbar_init(ptx::smem_u32(&b_afull[i]), 1);
+      ptx::mbar_init(ptx::smem_u32(&b_aempty[i]), 1 + (a.tw ? KS_NTAIL : 0));
+    }
+    for (int i = 0; i < KS_MAXS; ++i) {
+      ptx::mbar_init(ptx::smem_u32(&b_bfull[i]), 1);
+      ptx::mbar_init(ptx::smem_u32(&b_bempty[i]), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      ptx::mbar_init(ptx::smem_u32(&b_tfull[i]), 1);
+      ptx::mbar_init(ptx::smem_u32(&b_tempty[i]), 32 * KS_NEPI);
+    }
+    ptx::mbar_init(ptx::smem_u32(&b_fin), 1);
+    ptx::fence_mbar_init();
+    abort_sh = 0;
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = tmem_sh;
+  const int my_tiles =
+      blockIdx.x < (unsigned)a.ntiles ? (a.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int nkb = a.nkb, AS = a.AS, BS = a.BS;
+
+  if (warp == KS_W_TMA) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      ptx::prefetch_tmap(&tmA);
+      ptx::prefetch_tmap(&tmB);
+      const int np = a.split ? 2 : 1;
+      if (a.bres && my_tiles > 0) {
+        const uint32_t fb = ptx::smem_u32(&b_bfull[0]);
+        ptx::mbar_arrive_expect_tx(fb, (uint32_t)(nkb * bbytes));
+        for (int kb = 0; kb < nkb; ++kb)
+          for (int pl = 0; pl < np; ++pl)
+            ptx::tma_load_3d(ptx::smem_u32(bring + kb * bbytes + pl * a.Nc * 128), &tmB, kb * 64,
+                             0, pl, fb);
+      }
+      uint32_t g = 0, gb = 0;
+      for (int i = 0; i < my_tiles; ++i) {
+        const int line0 = (blockIdx.x + i * gridDim.x) * 128;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = (int)(g % AS);
+          if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_aempty[s]), ((g / AS) & 1) ^ 1, abort)) goto p_done;
+          const uint32_t fa = ptx::smem_u32(&b_afull[s]);
+          ptx::mbar_arrive_expect_tx(fa, (uint32_t)abytes);
+          for (int pl = 0; pl < np; ++pl)
+            ptx::tma_load_3d(ptx::smem_u32(aring + s * abytes + pl * KS_ABOX), &tmA, kb * 64,
+                             line0, pl, fa);
+          if (!a.bres) {
+            const int sb = (int)(gb % BS);
+            if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bempty[sb]), ((gb / BS) & 1) ^ 1, abort)) { ++g; goto p_done; }
+            const uint32_t fb = ptx::smem_u32(&b_bfull[sb]);
+            ptx::mbar_arrive_expect_tx(fb, (uint32_t)bbytes);
+            for (int pl = 0; pl < np; ++pl)
+              ptx::tma_load_3d(ptx::smem_u32(bring + sb * bbytes + pl * a.Nc * 128), &tmB,
+                               kb * 64, 0, pl, fb);
+            ++gb;
+          }
+        }
+      }
+    p_done:
+      // copies still in flight (only after an abort can any remain unconsumed)
+      for (uint32_t q = (g > (uint32_t)AS ? g - AS : 0u); q < g; ++q)
+        ptx::mbar_wait(ptx::smem_u32(&b_afull[q % AS]), (q / AS) & 1);
+      if (!a.bres)
+        for (uint32_t q = (gb > (uint32_t)BS ? gb - BS : 0u); q < gb; ++q)
+          ptx::mbar_wait(ptx::smem_u32(&b_bfull[q % BS]), (q / BS) & 1);
+      else if (my_tiles > 0)
+        ptx::mbar_wait(ptx::smem_u32(&b_bfull[0]), 0u);
+    }
+  } else if (warp == KS_W_MMA) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t id = ptx::idesc_bf16(128, a.Nc);
+      const uint32_t a0 = ptx::smem_u32(aring), b0 = ptx::smem_u32(bring);
+      const uint32_t blo = (uint32_t)a.Nc * 128u;               // B lo plane offset
+      uint32_t g = 0;
+      if (a.bres && my_tiles > 0 &&
+          !ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bfull[0]), 0u, abort)) goto m_done;
+      for (int i = 0; i < my_tiles; ++i) {
+        const int ab = i & 1;
+        const uint32_t use = (uint32_t)(i >> 1);
+        if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tempty[ab]), (use & 1) ^ 1, abort)) break;
+        ptx::tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(ab * a.Nc);
+        bool ok = true;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = (int)(g % AS);
+          const int sb = a.bres ? kb : (int)(g % BS);
+          if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_afull[s]), (g / AS) & 1, abort) ||
+              (!a.bres && !ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bfull[sb]), (g / BS) & 1, abort))) {
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t as = a0 + (uint32_t)(s * abytes), bs = b0 + (uint32_t)(sb * bbytes);
+          const int nst = min(4, a.nk - kb * 4);
+          for (int j = 0; j < nst; ++j) {
+            const uint64_t dAh = desc_sw128(as + 32u * j), dBh = desc_sw128(bs + 32u * j);
+            ptx::mma_bf16(d, dAh, dBh, id, (kb | j) ? 1u : 0u);
+            if (a.split) {
+              const uint64_t dAl = desc_sw128(as + (uint32_t)KS_ABOX + 32u * j);
+              const uint64_t dBl = desc_sw128(bs + blo + 32u * j);
+              ptx::mma_bf16(d, dAh, dBl, id, 1u);
+              ptx::mma_bf16(d, dAl, dBh, id, 1u);
+            }
+          }
+          ptx::mma_commit(ptx::smem_u32(&b_aempty[s]));
+          if (!a.bres) ptx::mma_commit(ptx::smem_u32(&b_bempty[sb]));
+        }
+        if (!ok) break;
+        ptx::mma_commit(ptx::smem_u32(&b_tfull[ab]));
+      }
+    m_done:
+      ptx::mma_commit(ptx::smem_u32(&b_fin));
+    }
+  } else if (warp >= KS_W_TAIL) {
+    // ------------------------------------------------------------ FP32 tail columns
+    if (a.tw) {
+      const int m = threadIdx.x - KS_W_TAIL * 32;             // line of the tile
+      const float4* gt = reinterpret_cast<const float4*>(a.tail);
+      float4* st = reinterpret_cast<float4*>(ttab);
+      for (int q = m; q < nkb * 64 * 2; q += KS_NTAIL) st[q] = __ldg(gt + q);
+      asm volatile("bar.sync 1, %0;" ::"n"(KS_NTAIL) : "memory");
+      const int sw = m & 7;
+      uint32_t g = 0;
+      bool ok = true;
+      for (int i = 0; i < my_tiles && ok; ++i) {
+        float acc[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = (int)(g % AS);
+          if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_afull[s]), (g / AS) & 1, abort)) { ok = false; break; }
+          // row m of the swizzled box: 16-byte chunk c (8 k values) stored at chunk c ^ (m % 8)
+          const uint8_t* hrow = aring + s * abytes + m * 128;
+          for (int c = 0; c < 8; ++c) {
+            float x[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[j] = 0.f;
+            add_bf8(*reinterpret_cast<const uint4*>(hrow + ((c ^ sw) << 4)), x);
+            if (a.split) add_bf8(*reinterpret_cast<const uint4*>(hrow + KS_ABOX + ((c ^ sw) << 4)), x);
+            const float4* tr = st + (kb * 64 + c * 8) * 2;
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+              const float4 t0 = tr[2 * kk], t1 = tr[2 * kk + 1];
+              acc[0] = fmaf(x[kk], t0.x, acc[0]);
+              acc[1] = fmaf(x[kk], t0.y, acc[1]);
+              acc[2] = fmaf(x[kk], t0.z, acc[2]);
+              acc[3] = fmaf(x[kk], t0.w, acc[3]);
+              acc[4] = fmaf(x[kk], t1.x, acc[4]);
+              acc[5] = fmaf(x[kk], t1.y, acc[5]);
+              acc[6] = fmaf(x[kk], t1.z, acc[6]);
+              acc[7] = fmaf(x[kk], t1.w, acc[7]);
+            }
+          }
+          ptx::mbar_arrive(ptx::smem_u32(&b_aempty[s]));
+        }
+        if (!ok) break;
+        const long long l = (long long)(blockIdx.x + i * gridDim.x) * 128 + m;
+        if (l < a.nlines) store_scalar(a.o, a.split, a.eps, out_base(a.o, l), 256, acc, a.tw);
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue (warps 2-9)
+    const int q = warp & 3;                          // TMEM lane quadrant of this warp
+    const int half = warp >= 6 ? 1 : 0;
+    const int nch = a.Nc / 16, nh = (nch + 1) / 2;
+    const int cbeg = half ? nh : 0, cend = half ? nch : nh;
+    const KsOut& o = a.o;
+    const int Lc = min(a.L, a.Nc);                   // valid tensor-core output columns
+    // row-wise outputs: columns written per row (split rows stop at the row pitch)
+    const int ncols = o.kind == KS_OUT_SPLIT ? min(a.Nc, (int)o.P) : Lc;
+    float* sg = stg + (warp - 2) * (32 * KS_SROW);
+    for (int i = 0; i < my_tiles; ++i) {
+      const int ab = i & 1;
+      const uint32_t use = (uint32_t)(i >> 1);
+      const long long l = (long long)(blockIdx.x + i * gridDim.x) * 128 + q * 32 + lane;
+      const bool valid = l < a.nlines;
+      // output address of (line l, column 0) and the symbol's (x, y) part
+      long long base = 0;
+      float sxy = 0.f;
+      if (valid) {
+        base = out_base(o, l);
+        if (o.sym) {
+          const int ry = (int)(l % a.Y), rx = (int)((l / a.Y) % a.X);
+          sxy = a.gamma + a.alpha * (a.lx[rx] + a.ly[ry]);
+        }
+      }
+      if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tfull[ab]), use & 1, abort)) break;
+      ptx::tc_fence_after();
+      const uint32_t trow = tmem + (uint32_t)(ab * a.Nc) + ((uint32_t)(q * 32) << 16);
+      for (int cp = cbeg; cp < cend; cp += 2) {
+        const int npair = min(2, cend - cp);
+        float v[32];
+        if (npair == 2) ptx::tmem_ld32(trow + (uint32_t)(cp * 16), v);
+        else ptx::tmem_ld16(trow + (uint32_t)(cp * 16), *reinterpret_cast<float(*)[16]>(v));
+#pragma unroll
+        for (int u2 = 0; u2 < 2; ++u2) {
+          if (u2 >= npair) break;
+          const int n0 = (cp + u2) * 16;
+          float* vc = v + 16 * u2;
+          if (o.sym && valid) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const float den = fmaf(a.alpha, __ldg(a.lz + min(n0 + j, a.L - 1)), sxy);
+              vc[j] = __fdividef(vc[j], den * den);
+            }
+          }
+          if (a.stage)   // whole warp: line0 = the warp's first line
+            store_rows_staged(o, a.split, a.eps, sg, lane, l - lane, a.nlines, n0, ncols, vc);
+          else if (valid)
+            store_scalar(o, a.split, a.eps, base, n0, vc, min(16, Lc - n0));
+        }
+      }
+      ptx::tc_fence_before();
+      ptx::mbar_arrive(ptx::smem_u32(&b_tempty[ab]));
+    }
+  }
+
+  // ------------------------------------------------------------ teardown
+  __syncthreads();
+  if (warp == KS_W_MMA) {
+    if (lane == 0) {
+      if (!ptx::mbar_wait(ptx::smem_u32(&b_fin), 0u)) abort_sh = 1;
+    }
+    __syncwarp();
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, 512u);
+  }
+  if (threadIdx.x == 0 && abort_sh) atomicExch(a.err, 3);
+}
+
+int g_ks_sms = 0;
+
+// fp32 rows [nrows][L] -> split field: one thread per (row, column), columns fastest.
+__global__ void k_split_rows(const float* __restrict__ in, long long nrows, int L, int split,
+                             KsOut o) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrows * L) return;
+  const long long l = i / L;
+  const int n = (int)(i - l * L);
+  const long long off = out_base(o, l) + (long long)n * o.G;
+  uint16_t h, lo;
+  split1(in[i], h, lo);
+  uint16_t* oh = reinterpret_cast<uint16_t*>(o.out);
+  oh[off] = h;
+  if (split) oh[o.plane + off] = lo;
+}
+
+}  // namespace
+
+int ks_pitch(int L) { return (L + 7) / 8 * 8; }
+
+bool ks_supported(const KPlan& kp) {
+  if (!tma_encode_fn() || !kp.ks[0][0] || !kp.ks[1][0] || !kp.ks[2][0]) return false;
+  if (kp.nx > 256 && !kp.kstail[0]) return false;
+  return kp.nx % 4 == 0 && kp.nx <= 264 && kp.ny <= 256 && kp.nz <= 256;
+}
+
+long long ks_field_floats(int nx, int ny, int nz, int ncomp) {
+  const long long X = nx, Y = ny, Z = nz;
+  const long long px = ks_pitch(nx), py = ks_pitch(ny), pz = ks_pitch(nz);
+  long long m = X * Y * Z;                      // fp32 rows
+  if (Z * Y * px > m) m = Z * Y * px;           // split [c][z][y][x] (x rows)
+  if (X * Z * py > m) m = X * Z * py;           // [c][x'][z][y] and [c][z][x'][y']
+  if (X * Y * pz > m) m = X * Y * pz;           // [c][x'][y'][z]
+  return m * ncomp;                             // two bf16 planes = one float per value
+}
+
+cudaError_t ks_split_rows(const float* in, long long nrows, int L, int split, const KsOut& o,
+                          cudaStream_t s) {
+  const long long n = nrows * L;
+  if (n > 0) k_split_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, nrows, L, split, o);
+  return cudaGetLastError();
+}
+
+// One pass of k_dft_ks over a split field `in` (hi plane, lo plane nlines*pitch elements later),
+// lines of length L along `axis` (0: x, 1: y, 2: z) with row pitch ks_pitch(L), output as `o`
+// says (eps: the update's step size for KS_OUT_UPD).
+cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, const void* in,
+                         long long nlines, const KsOut& o, float eps, cudaStream_t s) {
+  EncodeTiledFn enc = reinterpret_cast<EncodeTiledFn>(tma_encode_fn());
+  if (!enc) return cudaErrorNotSupported;
+  KsArgs a{};
+  a.L = axis == 0 ? kp.nx : axis == 1 ? kp.ny : kp.nz;
+  a.Nc = min(256, (a.L + 15) / 16 * 16);
+  a.tw = a.L > 256 ? a.L - 256 : 0;
+  if (a.tw > 8) return cudaErrorNotSupported;
+  a.nk = (a.L + 15) / 16;
+  a.nkb = (a.L + 63) / 64;
+  a.tail = a.tw ? kp.kstail[inverse ? 1 : 0] : nullptr;
+  a.split = split;
+  a.nlines = (int)nlines;
+  a.ntiles = (int)((nlines + 127) / 128);
+  a.o = o;
+  a.eps = eps;
+  // row-wise outputs (line l at l * P, consecutive columns) go through shared memory
+  a.stage = o.G == 1 ? 1 : 0;
+  if (a.stage && (o.D != 1 || o.E != 1 || o.F != 1)) return cudaErrorInvalidValue;
+  a.lx = kp.lx; a.ly = kp.ly; a.lz = kp.lz;
+  a.alpha = kp.alpha; a.gamma = kp.gamma;
+  a.X = kp.nx; a.Y = kp.ny;
+  a.err = kp.err;
+  const int P = ks_pitch(a.L);
+  const int np = split ? 2 : 1;
+  // A: [2 planes][nlines][P] bf16, box 64 k x 128 lines, 128-byte swizzle; k >= L and lines
+  // beyond the field read as zero
+  CUtensorMap tmA, tmB;
+  {
+    cuuint64_t dims[3] = {(cuuint64_t)a.L, (cuuint64_t)nlines, (cuuint64_t)np};
+    cuuint64_t strides[2] = {(cuuint64_t)P * 2, (cuuint64_t)nlines * P * 2};
+    cuuint32_t box[3] = {64, 128, 1}, es[3] = {1, 1, 1};
+    if (enc(&tmA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(in), dims, strides, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  // B: [2 planes][Nc][Kp] bf16 (zero padded), box 64 k x Nc rows
+  {
+    const int Kp = (a.L + 15) / 16 * 16;
+    cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)a.Nc, 2};
+    cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)a.Nc * Kp * 2};
+    cuuint32_t box[3] = {64, (cuuint32_t)a.Nc, 1}, es[3] = {1, 1, 1};
+    if (enc(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, kp.ks[axis][inverse ? 1 : 0], dims,
+            strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  // Shared memory (<= 225 KB): B resident when all its k-blocks fit next to 3 A stages;
+  // otherwise 3 A stages (2 when needed) and as many streamed B stages as fit (at least 2).
+  const int budget = 225 * 1024 - 1024 - ks_tbytes(a) - ks_sbytes(a);
+  const int ab = ks_abytes(split), bb = ks_bbytes(split, a.Nc);
+  if (a.nkb * bb + 3 * ab <= budget) {
+    a.bres = 1;
+    a.AS = min(KS_MAXS, (budget - a.nkb * bb) / ab);
+    a.BS = 1;
+  } else {
+    a.bres = 0;
+    a.AS = 3;
+    a.BS = min(KS_MAXS, (budget - 3 * ab) / bb);
+    if (a.BS < 2) {
+      a.AS = 2;
+      a.BS = min(KS_MAXS, (budget - 2 * ab) / bb);
+    }
+    if (a.BS < 2) return cudaErrorNotSupported;
+  }
+  const int smem = ks_smem(a);
+  cudaError_t e = cudaFuncSetAttribute(k_dft_ks, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (!g_ks_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_ks_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_ks_sms <= 0) g_ks_sms = 148;
+  }
+  const int grid = a.ntiles < g_ks_sms ? a.ntiles : g_ks_sms;
+  if (grid > 0) k_dft_ks<<<grid, KS_NT, smem, s>>>(tmA, tmB, a);
+  return cudaGetLastError();
+}
+
+}  // namespace lddmm

@@ -595,6 +595,8 @@ int g_num_sms = 0;
 
 }  // namespace
 
+void* tma_encode_fn() { return reinterpret_cast<void*>(encode_fn()); }
+
 bool tma_pass_supported(const KPlan& kp, int axis) {
   // TMA needs 16-byte row strides: the x extent (x and y passes) or the (y,x) plane (z pass)
   // must be a multiple of 4 floats.  Up to 512 accumulator columns (one TMEM buffer).

@@ -1,6 +1,7 @@
 // C ABI of liblddmm: context, buffers, the multiscale schedule and one gradient-descent
 // iteration of masked LDDMM (§2.4 of Kutten et al., SPIE 2016; Beg et al. 2005 update).
 // Host code only; every step of the computation runs in the kernels of kernels_*.cu.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -37,6 +38,7 @@ struct lddmm_ctx {
   std::vector<Level> levels;
   int cur = 0;
   int64_t Nmax = 0;
+  int64_t kcap = 0;         // floats in b and work (K's intermediate fields may pad rows)
   // working buffers, sized for the finest level
   float* v = nullptr;       // [T][3][N]
   float* v_tmp = nullptr;   // [T][3][N] resampling / backtracking copy
@@ -325,15 +327,18 @@ int run_step(lddmm_ctx* ctx) {
   launch_ereg(g, ctx->v, T, ctx->p.alpha, ctx->p.gamma, 1.0f / (L.hx * L.hx),
               1.0f / (L.hy * L.hy), 1.0f / (L.hz * L.hz), ctx->acc, s, ctx->st);
   hk(KID_EREG, 1);
-  // forward sweep j = 0 .. T-1 with smoothing and update
+  // forward sweep j = 0 .. T-1 with smoothing and update; on the pre-split K path the residual
+  // is written already split into bf16 hi/lo planes (the layout K's first product reads)
   const float c = 2.0f / (ctx->p.sigma * ctx->p.sigma);
+  const bool ks = ks_path(L.kp, ctx->p.k_mode, 3, ctx->kcap);
+  const int bsplit = ks ? (ctx->p.k_mode == LDDMM_K_BF16X3 ? 2 : 1) : 0;
   const float* uc = nullptr;
   int pf = 0;
   for (int j = 0; j < T; ++j) {
     void* vj = vptr(ctx, j, N);
     hk(KID_FWD_TERMS, 0);
     launch_fwd_terms(g, uc, L.I0, ctx->J1 + j * N, ctx->W + j * N, ctx->b, c, 1.0f / L.hx,
-                     1.0f / L.hy, 1.0f / L.hz, s, ctx->st);
+                     1.0f / L.hy, 1.0f / L.hz, s, ctx->st, bsplit, ks_pitch(g.nx));
     hk(KID_FWD_TERMS, 1);
     float* unx = ctx->uF[pf];
     hk(KID_FWD_FLOW, 0);
@@ -343,9 +348,11 @@ int run_step(lddmm_ctx* ctx) {
     // K b_j and the update v_j <- v_j - eps (2 v_j - K b_j): fused into the last DFT pass for
     // float storage, a separate pass for bf16 storage
     if (ctx->st == 0) {
-      CK(apply_K(L.kp, ctx->p.k_mode, ctx->b, ctx->b, ctx->work, 3, s, hk, (float*)vj, ctx->eps));
+      CK(apply_K(L.kp, ctx->p.k_mode, ctx->b, ctx->b, ctx->work, 3, s, hk, (float*)vj, ctx->eps,
+                 ctx->kcap, ks));
     } else {
-      CK(apply_K(L.kp, ctx->p.k_mode, ctx->b, ctx->b, ctx->work, 3, s, hk));
+      CK(apply_K(L.kp, ctx->p.k_mode, ctx->b, ctx->b, ctx->work, 3, s, hk, nullptr, 0.f,
+                 ctx->kcap, ks));
       hk(KID_UPDATE, 0);
       launch_update(g, vj, ctx->b, ctx->eps, s, ctx->st);
       hk(KID_UPDATE, 1);
@@ -515,6 +522,11 @@ int lddmm_create(const lddmm_params* p, const float* I0, const float* I1, const 
   }
   const int64_t N = ctx->levels.back().g.N;
   ctx->Nmax = N;
+  ctx->kcap = 3 * N;
+  for (int l = 0; l < nl; ++l) {
+    const Grid& g = ctx->levels[l].g;
+    ctx->kcap = std::max<int64_t>(ctx->kcap, ks_field_floats(g.nx, g.ny, g.nz, 3));
+  }
   const int64_t T = p->T;
   auto A = [&](cudaError_t e) {
     if (e != cudaSuccess) {
@@ -535,8 +547,8 @@ int lddmm_create(const lddmm_params* p, const float* I0, const float* I1, const 
   ok = ok && A(dalloc(&ctx->v, ve)) && A(dalloc(&ctx->v_tmp, ve)) &&
        A(dalloc(&ctx->uB[0], 3 * N)) && A(dalloc(&ctx->uB[1], 3 * N)) &&
        A(dalloc(&ctx->uF[0], 3 * N)) && A(dalloc(&ctx->uF[1], 3 * N)) &&
-       A(dalloc(&ctx->J1, T * N)) && A(dalloc(&ctx->W, T * N)) && A(dalloc(&ctx->b, 3 * N)) &&
-       A(dalloc(&ctx->work, 3 * N)) && A(dalloc(&ctx->J0T, N)) && A(dalloc(&ctx->stage, 3 * N)) &&
+       A(dalloc(&ctx->J1, T * N)) && A(dalloc(&ctx->W, T * N)) && A(dalloc(&ctx->b, ctx->kcap)) &&
+       A(dalloc(&ctx->work, ctx->kcap)) && A(dalloc(&ctx->J0T, N)) && A(dalloc(&ctx->stage, 3 * N)) &&
        A(dalloc(&ctx->acc, 1)) && A(dalloc(&ctx->flag, 1)) && A(dalloc(&ctx->hist, 3 * 65536)) &&
        A(cudaMallocHost((void**)&ctx->acc_host, sizeof(Acc)));
   if (ok && (p->flags & 1)) ok = A(dalloc(&ctx->v_prev, ve));
@@ -696,7 +708,8 @@ int lddmm_apply_K(lddmm_ctx* ctx, const float* src, float* dst) {
   const Level& L = ctx->levels[ctx->cur];
   const int64_t N = L.g.N;
   CK(cudaMemcpyAsync(ctx->stage, src, N * sizeof(float), cudaMemcpyDefault, ctx->stream));
-  CK(apply_K(L.kp, ctx->p.k_mode, ctx->stage, ctx->stage, ctx->work, 1, ctx->stream));
+  CK(apply_K(L.kp, ctx->p.k_mode, ctx->stage, ctx->stage, ctx->work, 1, ctx->stream, Hook(),
+             nullptr, 0.f, std::min<int64_t>(3 * ctx->Nmax, ctx->kcap)));
   return copy_out(ctx, dst, ctx->stage, N * sizeof(float));
 }
 

@@ -59,7 +59,13 @@ PROD = K_MODES[MODES[-1]][0]   # the mode the benchmark runs
                                                  ((2, 3, 5), (1, 1, 1), 1.0, 1.0),
                                                  # x lengths past 256: FP32 tail columns
                                                  ((6, 5, 264), (1, 1, 1), 0.02, 1.0),
-                                                 ((4, 7, 260), (1, 1, 1), 0.3, 1.2)])
+                                                 ((4, 7, 260), (1, 1, 1), 0.3, 1.2),
+                                                 # y/z passes on split fields: several
+                                                 # k-blocks, resident and streamed B, and
+                                                 # padded rows (z = 100, 230)
+                                                 ((100, 72, 64), (1, 1, 1), 0.3, 1.0),
+                                                 ((40, 200, 32), (1, 1, 1), 0.3, 1.0),
+                                                 ((230, 24, 16), (1, 1, 1), 0.3, 1.0)])
 def test_K_matches_oracle(L, O, mode, shape, h, alpha, gamma):
     code, tol = K_MODES[mode]
     rng = np.random.default_rng(1)
