@@ -57,7 +57,6 @@ struct KsArgs {
   const float* tail;   // their table B(k, 256 + j) as float [nkb * 64][8], zero padded
   KsOut o;             // output addressing
   float eps;           // KS_OUT_UPD: step size
-  int stage;           // 1: row-wise output (o.G == 1), staged through shared memory
   const float* lx;     // symbol (o.sym): lambda per x, y, z frequency
   const float* ly;
   const float* lz;
@@ -72,7 +71,7 @@ __host__ __device__ inline int ks_tbytes(const KsArgs& a) { return a.tw ? a.nkb 
 // per epilogue warp: 32 lines x 16 columns of fp32, rows padded to 17 (conflict-free transpose)
 constexpr int KS_SROW = 17;
 __host__ __device__ inline int ks_sbytes(const KsArgs& a) {
-  return a.stage ? KS_NEPI * 32 * KS_SROW * 4 : 0;
+  return a.o.G == 1 ? KS_NEPI * 32 * KS_SROW * 4 : 0;
 }
 __host__ __device__ inline int ks_smem(const KsArgs& a) {
   return 1024 + a.AS * ks_abytes(a.split) + (a.bres ? a.nkb : a.BS) * ks_bbytes(a.split, a.Nc) +
@@ -113,85 +112,113 @@ __device__ __forceinline__ void add_bf8(uint4 w, float* x) {
   }
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Element offset of (line l, column 0): l = (a D + b) E + e -> (a F + b) P + e.
 __device__ __forceinline__ long long out_base(const KsOut& o, long long l) {
   const long long e = l % o.E, t = l / o.E;
   return (t / o.D * o.F + t % o.D) * o.P + e;
 }
 
-// Store cnt consecutive output columns n0.. of one line, one element at a time (transposed
-// outputs and the FP32 tail columns).
+// Store cnt (<= NMAX) consecutive output columns n0.. of one line, one element at a time
+// (transposed outputs whose runs are not vector aligned, and the FP32 tail columns).  The loops
+// are unrolled over NMAX so that vc stays in registers.
+template <int NMAX>
 __device__ __forceinline__ void store_scalar(const KsOut& o, int split, float eps, long long base,
                                              int n0, const float* vc, int cnt) {
   if (o.kind == KS_OUT_SPLIT) {
     uint16_t* oh = reinterpret_cast<uint16_t*>(o.out);
-    for (int j = 0; j < cnt; ++j) {
-      uint16_t h, lo;
-      split1(vc[j], h, lo);
-      const long long off = base + (long long)(n0 + j) * o.G;
-      oh[off] = h;
-      if (split) oh[o.plane + off] = lo;
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j) {
+      if (j < cnt) {
+        uint16_t h, lo;
+        split1(vc[j], h, lo);
+        const long long off = base + (long long)(n0 + j) * o.G;
+        oh[off] = h;
+        if (split) oh[o.plane + off] = lo;
+      }
     }
   } else {
     float* of = reinterpret_cast<float*>(o.out);
-    for (int j = 0; j < cnt; ++j) {
-      const long long off = base + (long long)(n0 + j) * o.G;
-      if (o.kind == KS_OUT_UPD) {
-        const float w = of[off];
-        of[off] = w - eps * (2.f * w - vc[j]);
-      } else {
-        of[off] = vc[j];
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j) {
+      if (j < cnt) {
+        const long long off = base + (long long)(n0 + j) * o.G;
+        if (o.kind == KS_OUT_UPD) {
+          const float w = of[off];
+          of[off] = w - eps * (2.f * w - vc[j]);
+        } else {
+          of[off] = vc[j];
+        }
       }
     }
   }
 }
 
-// Row-wise output of 16 columns n0.. for the 32 lines line0.. of one warp (lane = line on
-// entry): the values go through the warp's shared-memory tile so that each store instruction
-// writes two 16-column segments of two rows (rows of o.P elements, line l at l * o.P).
-__device__ __forceinline__ void store_rows_staged(const KsOut& o, int split, float eps,
-                                                  float* sg, int lane, long long line0,
-                                                  long long nlines, int n0, int ncols,
-                                                  const float* vc) {
+__device__ __forceinline__ uint32_t pack_bf16x2(uint16_t a, uint16_t b) {
+  return (uint32_t)a | ((uint32_t)b << 16);
+}
+
+// Row-wise outputs (o.G == 1, line l at l * o.P): the 16 columns n0.. of the warp's 32 lines
+// line0.. (lane = line on entry) leave through the warp's shared-memory tile, so that a lane
+// writes 8 consecutive bf16 columns (split, 16-byte stores) or 4 consecutive fp32 columns
+// (plain or the update, 16-byte loads and stores) of one line, and a store instruction covers
+// 16 or 8 lines.  (Transposed outputs, consecutive lines = consecutive positions, are already
+// coalesced across the lanes and are stored element by element from registers.)
+__device__ __forceinline__ void store_rows(const KsOut& o, int split, float eps, float* sg,
+                                           int lane, long long line0, long long nlines, int n0,
+                                           int ncols, const float* vc) {
 #pragma unroll
   for (int j = 0; j < 16; ++j) sg[lane * KS_SROW + j] = vc[j];
   __syncwarp();
-  const int jj = lane & 15, rh = lane >> 4;
-  const int n = n0 + jj;
-  if (o.kind == KS_OUT_UPD) {
-    float* of = reinterpret_cast<float*>(o.out);
-    float old[16];
-#pragma unroll
-    for (int it = 0; it < 16; ++it) {
-      const long long l = line0 + 2 * it + rh;
-      old[it] = (l < nlines && n < ncols) ? of[l * o.P + n] : 0.f;
-    }
-#pragma unroll
-    for (int it = 0; it < 16; ++it) {
-      const int r = 2 * it + rh;
-      const long long l = line0 + r;
-      if (l < nlines && n < ncols)
-        of[l * o.P + n] = old[it] - eps * (2.f * old[it] - sg[r * KS_SROW + jj]);
-    }
-  } else if (o.kind == KS_OUT_F32) {
-    float* of = reinterpret_cast<float*>(o.out);
-#pragma unroll
-    for (int it = 0; it < 16; ++it) {
-      const int r = 2 * it + rh;
-      const long long l = line0 + r;
-      if (l < nlines && n < ncols) of[l * o.P + n] = sg[r * KS_SROW + jj];
-    }
-  } else {
+  if (o.kind == KS_OUT_SPLIT) {
     uint16_t* oh = reinterpret_cast<uint16_t*>(o.out);
 #pragma unroll
-    for (int it = 0; it < 16; ++it) {
-      const int r = 2 * it + rh;
+    for (int it = 0; it < 2; ++it) {
+      const int idx = it * 32 + lane, r = idx >> 1, c8 = (idx & 1) * 8;
       const long long l = line0 + r;
-      if (l < nlines && n < ncols) {
-        uint16_t h, lo;
-        split1(sg[r * KS_SROW + jj], h, lo);
-        oh[l * o.P + n] = h;
-        if (split) oh[o.plane + l * o.P + n] = lo;
+      if (l < nlines && n0 + c8 + 8 <= ncols) {
+        uint16_t h[8], lo[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) split1(sg[r * KS_SROW + c8 + k], h[k], lo[k]);
+        const long long off = l * o.P + n0 + c8;
+        *reinterpret_cast<uint4*>(oh + off) =
+            make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]), pack_bf16x2(h[4], h[5]),
+                       pack_bf16x2(h[6], h[7]));
+        if (split)
+          *reinterpret_cast<uint4*>(oh + o.plane + off) =
+              make_uint4(pack_bf16x2(lo[0], lo[1]), pack_bf16x2(lo[2], lo[3]),
+                         pack_bf16x2(lo[4], lo[5]), pack_bf16x2(lo[6], lo[7]));
+      }
+    }
+  } else {
+    float* of = reinterpret_cast<float*>(o.out);
+    float4 old[4];
+    if (o.kind == KS_OUT_UPD) {
+#pragma unroll
+      for (int it = 0; it < 4; ++it) {
+        const int idx = it * 32 + lane, r = idx >> 2, c4 = (idx & 3) * 4;
+        const long long l = line0 + r;
+        if (l < nlines && n0 + c4 + 4 <= ncols)
+          old[it] = *reinterpret_cast<const float4*>(of + l * o.P + n0 + c4);
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      const int idx = it * 32 + lane, r = idx >> 2, c4 = (idx & 3) * 4;
+      const long long l = line0 + r;
+      if (l < nlines && n0 + c4 + 4 <= ncols) {
+        const float* q = sg + r * KS_SROW + c4;
+        float4 w = make_float4(q[0], q[1], q[2], q[3]);
+        if (o.kind == KS_OUT_UPD) {
+          const float4 p = old[it];
+          w = make_float4(p.x - eps * (2.f * p.x - w.x), p.y - eps * (2.f * p.y - w.y),
+                          p.z - eps * (2.f * p.z - w.z), p.w - eps * (2.f * p.w - w.w));
+        }
+        *reinterpret_cast<float4*>(of + l * o.P + n0 + c4) = w;
       }
     }
   }
@@ -351,6 +378,10 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
       uint32_t g = 0;
       bool ok = true;
       for (int i = 0; i < my_tiles && ok; ++i) {
+        const long long lt = (long long)(blockIdx.x + i * gridDim.x) * 128 + m;
+        if (a.o.kind == KS_OUT_UPD && lt < a.nlines)      // the old v of the tail columns
+          prefetch_l2(reinterpret_cast<const float*>(a.o.out) + lt * a.o.P + 256,
+                      (uint32_t)a.tw * 4u);   // tw = 4 or 8: x lengths are multiples of 4
         float acc[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[j] = 0.f;
@@ -383,7 +414,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
         }
         if (!ok) break;
         const long long l = (long long)(blockIdx.x + i * gridDim.x) * 128 + m;
-        if (l < a.nlines) store_scalar(a.o, a.split, a.eps, out_base(a.o, l), 256, acc, a.tw);
+        if (l < a.nlines) store_scalar<8>(a.o, a.split, a.eps, out_base(a.o, l), 256, acc, a.tw);
       }
     }
   } else {
@@ -394,8 +425,8 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
     const int cbeg = half ? nh : 0, cend = half ? nch : nh;
     const KsOut& o = a.o;
     const int Lc = min(a.L, a.Nc);                   // valid tensor-core output columns
-    // row-wise outputs: columns written per row (split rows stop at the row pitch)
-    const int ncols = o.kind == KS_OUT_SPLIT ? min(a.Nc, (int)o.P) : Lc;
+    // columns written per line (row-wise split outputs stop at the row pitch)
+    const int ncols = (o.G == 1 && o.kind == KS_OUT_SPLIT) ? min(a.Nc, (int)o.P) : Lc;
     float* sg = stg + (warp - 2) * (32 * KS_SROW);
     for (int i = 0; i < my_tiles; ++i) {
       const int ab = i & 1;
@@ -411,6 +442,15 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
           const int ry = (int)(l % a.Y), rx = (int)((l / a.Y) % a.X);
           sxy = a.gamma + a.alpha * (a.lx[rx] + a.ly[ry]);
         }
+      }
+      const long long line0 = l - lane;
+      // the update reads the old v of this warp's columns: start bringing it into L2 while the
+      // tensor cores are still on the tile
+      if (o.kind == KS_OUT_UPD && valid && cend * 16 > cbeg * 16) {
+        const int c1 = min(cend * 16, Lc);
+        if (c1 > cbeg * 16)
+          prefetch_l2(reinterpret_cast<const float*>(o.out) + l * o.P + cbeg * 16,
+                      (uint32_t)(c1 - cbeg * 16) * 4u);
       }
       if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tfull[ab]), use & 1, abort)) break;
       ptx::tc_fence_after();
@@ -432,10 +472,10 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
               vc[j] = __fdividef(vc[j], den * den);
             }
           }
-          if (a.stage)   // whole warp: line0 = the warp's first line
-            store_rows_staged(o, a.split, a.eps, sg, lane, l - lane, a.nlines, n0, ncols, vc);
+          if (o.G == 1)   // whole warp
+            store_rows(o, a.split, a.eps, sg, lane, line0, a.nlines, n0, ncols, vc);
           else if (valid)
-            store_scalar(o, a.split, a.eps, base, n0, vc, min(16, Lc - n0));
+            store_scalar<16>(o, a.split, a.eps, base, n0, vc, min(16, Lc - n0));
         }
       }
       ptx::tc_fence_before();
@@ -520,9 +560,8 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
   a.ntiles = (int)((nlines + 127) / 128);
   a.o = o;
   a.eps = eps;
-  // row-wise outputs (line l at l * P, consecutive columns) go through shared memory
-  a.stage = o.G == 1 ? 1 : 0;
-  if (a.stage && (o.D != 1 || o.E != 1 || o.F != 1)) return cudaErrorInvalidValue;
+  // row-wise outputs: line l at l * P (P a multiple of 8 bf16 or 4 floats)
+  if (o.G == 1 && (o.D != 1 || o.E != 1 || o.F != 1)) return cudaErrorInvalidValue;
   a.lx = kp.lx; a.ly = kp.ly; a.lz = kp.lz;
   a.alpha = kp.alpha; a.gamma = kp.gamma;
   a.X = kp.nx; a.Y = kp.ny;
@@ -552,11 +591,11 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
-  // Shared memory (<= 225 KB): B resident when all its k-blocks fit next to 3 A stages;
+  // Shared memory (<= 225 KB): B resident when all its k-blocks fit next to 2 A stages;
   // otherwise 3 A stages (2 when needed) and as many streamed B stages as fit (at least 2).
   const int budget = 225 * 1024 - 1024 - ks_tbytes(a) - ks_sbytes(a);
   const int ab = ks_abytes(split), bb = ks_bbytes(split, a.Nc);
-  if (a.nkb * bb + 3 * ab <= budget) {
+  if (a.nkb * bb + 2 * ab <= budget) {
     a.bres = 1;
     a.AS = min(KS_MAXS, (budget - a.nkb * bb) / ab);
     a.BS = 1;
