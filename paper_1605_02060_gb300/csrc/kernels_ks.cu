@@ -168,9 +168,23 @@ __device__ __forceinline__ uint32_t pack_bf16x2(uint16_t a, uint16_t b) {
 // (plain or the update, 16-byte loads and stores) of one line, and a store instruction covers
 // 16 or 8 lines.  (Transposed outputs, consecutive lines = consecutive positions, are already
 // coalesced across the lanes and are stored element by element from registers.)
+// The old v that the update combines with the 16 columns n0.. of the warp's 32 lines, in the
+// lane order store_rows uses (4 consecutive fp32 columns of one line per 16-byte load).
+__device__ __forceinline__ void load_old_rows(const KsOut& o, int lane, long long line0,
+                                              long long nlines, int n0, int ncols, float4* old) {
+  const float* of = reinterpret_cast<const float*>(o.out);
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int idx = it * 32 + lane, r = idx >> 2, c4 = (idx & 3) * 4;
+    const long long l = line0 + r;
+    if (l < nlines && n0 + c4 + 4 <= ncols)
+      old[it] = *reinterpret_cast<const float4*>(of + l * o.P + n0 + c4);
+  }
+}
+
 __device__ __forceinline__ void store_rows(const KsOut& o, int split, float eps, float* sg,
                                            int lane, long long line0, long long nlines, int n0,
-                                           int ncols, const float* vc) {
+                                           int ncols, const float* vc, const float4* old) {
 #pragma unroll
   for (int j = 0; j < 16; ++j) sg[lane * KS_SROW + j] = vc[j];
   __syncwarp();
@@ -196,16 +210,6 @@ __device__ __forceinline__ void store_rows(const KsOut& o, int split, float eps,
     }
   } else {
     float* of = reinterpret_cast<float*>(o.out);
-    float4 old[4];
-    if (o.kind == KS_OUT_UPD) {
-#pragma unroll
-      for (int it = 0; it < 4; ++it) {
-        const int idx = it * 32 + lane, r = idx >> 2, c4 = (idx & 3) * 4;
-        const long long l = line0 + r;
-        if (l < nlines && n0 + c4 + 4 <= ncols)
-          old[it] = *reinterpret_cast<const float4*>(of + l * o.P + n0 + c4);
-      }
-    }
 #pragma unroll
     for (int it = 0; it < 4; ++it) {
       const int idx = it * 32 + lane, r = idx >> 2, c4 = (idx & 3) * 4;
@@ -452,11 +456,21 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
           prefetch_l2(reinterpret_cast<const float*>(o.out) + l * o.P + cbeg * 16,
                       (uint32_t)(c1 - cbeg * 16) * 4u);
       }
+      float4 oldv[8];
+      if (o.kind == KS_OUT_UPD && cbeg < cend) {
+        load_old_rows(o, lane, line0, a.nlines, cbeg * 16, ncols, oldv);
+        if (cbeg + 1 < cend) load_old_rows(o, lane, line0, a.nlines, cbeg * 16 + 16, ncols, oldv + 4);
+      }
       if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tfull[ab]), use & 1, abort)) break;
       ptx::tc_fence_after();
       const uint32_t trow = tmem + (uint32_t)(ab * a.Nc) + ((uint32_t)(q * 32) << 16);
       for (int cp = cbeg; cp < cend; cp += 2) {
         const int npair = min(2, cend - cp);
+        if (o.kind == KS_OUT_UPD && cp > cbeg) {
+          // the old v of this pair of chunks (the first pair was requested before the wait)
+          load_old_rows(o, lane, line0, a.nlines, cp * 16, ncols, oldv);
+          if (npair == 2) load_old_rows(o, lane, line0, a.nlines, cp * 16 + 16, ncols, oldv + 4);
+        }
         float v[32];
         if (npair == 2) ptx::tmem_ld32(trow + (uint32_t)(cp * 16), v);
         else ptx::tmem_ld16(trow + (uint32_t)(cp * 16), *reinterpret_cast<float(*)[16]>(v));
@@ -473,7 +487,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
             }
           }
           if (o.G == 1)   // whole warp
-            store_rows(o, a.split, a.eps, sg, lane, line0, a.nlines, n0, ncols, vc);
+            store_rows(o, a.split, a.eps, sg, lane, line0, a.nlines, n0, ncols, vc, oldv + 4 * u2);
           else if (valid)
             store_scalar<16>(o, a.split, a.eps, base, n0, vc, min(16, Lc - n0));
         }
