@@ -4,3 +4,4 @@ TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the b
 CPU-baseline leg.  The library never imports it; it shares no code with the CUDA path.
 """
 from . import lddmm  # noqa: F401
+from . import metrics  # noqa: F401
