@@ -354,7 +354,8 @@ def _time_steps(L, params, I0, I1, M, stream, warm=2, steps=5):
 
 def measure_extras(L, I0, I1, M, stream, dev):
     """Secondary measurements reported beside the headline: the same iteration with the other
-    precision settings, and the exact-gradient (adjoint) evaluation on a 128^3 pair."""
+    precision settings, the exact-gradient (adjoint) evaluation on a 128^3 pair, and the
+    surface distances of §2.7 at the benchmark's grid."""
     import numpy as np
     import torch
 
@@ -383,6 +384,26 @@ def measure_extras(L, I0, I1, M, stream, dev):
         torch.cuda.synchronize()
         out[name] = round(e0.elapsed_time(e1) / 3, 3)
         ctx.close()
+    # §2.7 surface measures at the benchmark's grid: the atlas mask after 20 iterations, pulled to
+    # target space by its labels, against the target mask (wall time of the C call, host waits)
+    p = L.default_params(X, Y, Z, T=T)
+    ctx = L.Lddmm(p, I0, I1, M, stream=stream)
+    for _ in range(20):
+        ctx.step(want_energy=False)
+    lab = ctx.transfer_labels((I0 > 0.5).to(torch.int16), torch.empty_like(I0, dtype=torch.int16))
+    A = (lab != 0).to(torch.uint8)
+    B = (I1 > 0.5).to(torch.uint8)
+    A0 = (I0 > 0.5).to(torch.uint8)
+    ctx.surface_distance(A0, B)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hd0, md0, _, _ = ctx.surface_distance(A0, B)
+    hd, md, na, nb = ctx.surface_distance(A, B)
+    dt = (time.perf_counter() - t0) / 2
+    ctx.close()
+    out["surface_distance"] = {"ms": round(1000 * dt, 2), "surface_voxels": [na, nb],
+                               "hausdorff_before": hd0, "median_before": md0,
+                               "hausdorff_after_20_iters": hd, "median_after_20_iters": md}
     return out
 
 

@@ -158,6 +158,26 @@ int lddmm_energy_grad(lddmm_ctx* ctx, const float* v, float* grad, double* E);
 /* Mean Dice overlap over labels > 0 present in A or B (uint16, n voxels each). */
 int lddmm_dice(lddmm_ctx* ctx, const uint16_t* A, const uint16_t* B, int64_t n, double* out);
 
+/* Surface distances between two binary masks on the current level's grid (§2.7: the Hausdorff
+ * distance d_H and the median surface distance d_M between the deformed-template surface
+ * S(1) = boundary(M0 o phi^-1) and the target surface S1 = boundary(M1)).
+ * A, B: uint8 [nz][ny][nx] (nonzero = inside), device or host memory, read only.  A surface
+ * voxel is a mask voxel with a face neighbour outside the mask (outside the grid counts).
+ * Distances are Euclidean between voxel centres in physical units (the level's spacing).
+ * out[0] = d_H = max of both directed maxima; out[1] = d_M = median of the union of the directed
+ * distances of S_A to S_B and of S_B to S_A (mean of the two middle values for an even count);
+ * out[2], out[3] = the number of surface voxels of A and of B.  Host memory.
+ * Allocates scratch for the surface lists and distances for the duration of the call and waits
+ * for the result (bounded).  LDDMM_ERR_INVALID_ARG when a mask has no surface voxel. */
+int lddmm_surface_distance(lddmm_ctx* ctx, const uint8_t* A, const uint8_t* B, double out[4]);
+
+/* Landmark errors e_k = |phi(x_k) - y_k| (§2.7) for the current v: phi(x) = x + u01(x) carries
+ * a template point to the target point it lands on (u01 = phi_{0,1} - id interpolated
+ * trilinearly, clamp to edge).  xk, yk: n points as float [n][3] = (x, y, z) in voxel
+ * coordinates of the current level; err: n doubles, physical units.  Any pointer may be device
+ * or host memory; a host err is written before the call returns. */
+int lddmm_landmark_error(lddmm_ctx* ctx, const float* xk, const float* yk, int n, double* err);
+
 /* Per-kernel device time, summed over the launches since lddmm_profile_start. */
 typedef struct {
   char name[32];

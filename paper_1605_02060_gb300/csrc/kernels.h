@@ -78,6 +78,21 @@ void launch_fill(float* a, int64_t n, float value, cudaStream_t s);
 void launch_dice_hist(const uint16_t* A, const uint16_t* B, int64_t n,
                       unsigned long long* hist /* 3 x 65536 */, cudaStream_t s);
 
+// ---- registration-quality measures of §2.7 (kernels_metrics.cu) ----
+// Surface voxels of mask m appended to list as (x, y, z, 0); *count receives their number
+// (entries past cap are counted but not written, so cap = 0 only counts).
+cudaError_t surface_list(const Grid& g, const uint8_t* m, int4* list, unsigned* count,
+                         unsigned cap, cudaStream_t s);
+// d[i] = distance (physical units) from src[i] to the nearest point of dst.
+cudaError_t nearest_distances(const int4* src, unsigned ns, const int4* dst, unsigned nd,
+                              float hx, float hy, float hz, double* d, cudaStream_t s);
+// out[0] = max of d[0..n), out[1] = k1-th, out[2] = k2-th smallest (0-based); one block.
+cudaError_t order_stats(const double* d, unsigned n, unsigned k1, unsigned k2, double* out,
+                        cudaStream_t s);
+// e[k] = |(x_k + u01(x_k) - y_k) h| for n points (float [n][3], voxel coordinates).
+cudaError_t landmark_errors(const Grid& g, const float* u01, const float* xk, const float* yk,
+                            int n, float hx, float hy, float hz, double* e, cudaStream_t s);
+
 // ---- exact gradient of the discrete energy (kernels_adjoint.cu) ----
 void launch_adj_init(const Grid& g, const float* uT, const float* I0, const float* I1,
                      const float* M, float* gT, float scale, cudaStream_t s);

@@ -751,6 +751,96 @@ int lddmm_dice(lddmm_ctx* ctx, const uint16_t* A, const uint16_t* B, int64_t n, 
   return LDDMM_OK;
 }
 
+int lddmm_surface_distance(lddmm_ctx* ctx, const uint8_t* A, const uint8_t* B, double out[4]) {
+  if (!ctx || !A || !B || !out) return fail(ctx, LDDMM_ERR_INVALID_ARG, "NULL argument");
+  const Level& L = ctx->levels[ctx->cur];
+  const Grid& g = L.g;
+  cudaStream_t s = ctx->stream;
+  // scratch: host masks, the two counters, then the lists and distances once sized
+  uint8_t* mk = nullptr;
+  unsigned* cnt = nullptr;
+  int4* list = nullptr;
+  double* d = nullptr;
+  double* st = nullptr;
+  auto done = [&](int rc) {
+    cudaStreamSynchronize(s);
+    cudaFree(mk); cudaFree(cnt); cudaFree(list); cudaFree(d); cudaFree(st);
+    cudaGetLastError();
+    return rc;
+  };
+  const uint8_t* ma = A;
+  const uint8_t* mb = B;
+  const bool da = is_device_ptr(A), db = is_device_ptr(B);
+  if (cudaMalloc((void**)&cnt, 2 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc((void**)&st, 3 * sizeof(double)) != cudaSuccess)
+    return done(fail(ctx, LDDMM_ERR_OOM, "device allocation failed"));
+  if (!da || !db) {
+    if (cudaMalloc((void**)&mk, 2 * (size_t)g.N) != cudaSuccess)
+      return done(fail(ctx, LDDMM_ERR_OOM, "device allocation failed"));
+    if (!da) { cudaMemcpyAsync(mk, A, g.N, cudaMemcpyDefault, s); ma = mk; }
+    if (!db) { cudaMemcpyAsync(mk + g.N, B, g.N, cudaMemcpyDefault, s); mb = mk + g.N; }
+  }
+  // count the surface voxels, then list them
+  unsigned h[2] = {0, 0};
+  cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned), s);
+  surface_list(g, ma, nullptr, cnt, 0u, s);
+  surface_list(g, mb, nullptr, cnt + 1, 0u, s);
+  cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s);
+  int rc = wait_stream(ctx);
+  if (rc) return done(rc);
+  if (cudaGetLastError() != cudaSuccess) return done(fail(ctx, LDDMM_ERR_CUDA, "surface count failed"));
+  if (h[0] == 0 || h[1] == 0) return done(fail(ctx, LDDMM_ERR_INVALID_ARG, "a mask has no surface voxel"));
+  const unsigned na = h[0], nb = h[1];
+  if (cudaMalloc((void**)&list, (size_t)(na + nb) * sizeof(int4)) != cudaSuccess ||
+      cudaMalloc((void**)&d, (size_t)(na + nb) * sizeof(double)) != cudaSuccess)
+    return done(fail(ctx, LDDMM_ERR_OOM, "device allocation failed"));
+  cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned), s);
+  surface_list(g, ma, list, cnt, na, s);
+  surface_list(g, mb, list + na, cnt + 1, nb, s);
+  nearest_distances(list, na, list + na, nb, L.hx, L.hy, L.hz, d, s);
+  nearest_distances(list + na, nb, list, na, L.hx, L.hy, L.hz, d + na, s);
+  const unsigned n = na + nb;
+  order_stats(d, n, (n - 1) / 2, n / 2, st, s);
+  double r[3];
+  cudaMemcpyAsync(r, st, sizeof(r), cudaMemcpyDeviceToHost, s);
+  if (cudaGetLastError() != cudaSuccess) return done(fail(ctx, LDDMM_ERR_CUDA, "surface distance launch failed"));
+  rc = wait_stream(ctx);
+  if (rc) return done(rc);
+  out[0] = r[0];
+  out[1] = 0.5 * (r[1] + r[2]);
+  out[2] = (double)na;
+  out[3] = (double)nb;
+  return done(LDDMM_OK);
+}
+
+int lddmm_landmark_error(lddmm_ctx* ctx, const float* xk, const float* yk, int n, double* err) {
+  if (!ctx || !xk || !yk || !err || n < 0) return fail(ctx, LDDMM_ERR_INVALID_ARG, "bad argument");
+  if (n == 0) return LDDMM_OK;
+  int rc;
+  if (!ctx->maps_valid && (rc = refresh_maps(ctx, false))) return rc;
+  const Level& L = ctx->levels[ctx->cur];
+  cudaStream_t s = ctx->stream;
+  float* pts = nullptr;
+  double* e = nullptr;
+  const bool dx = is_device_ptr(xk), dy = is_device_ptr(yk), de = is_device_ptr(err);
+  if (cudaMalloc((void**)&pts, (size_t)6 * n * sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&e, (size_t)n * sizeof(double)) != cudaSuccess) {
+    cudaFree(pts);
+    cudaGetLastError();
+    return fail(ctx, LDDMM_ERR_OOM, "device allocation failed");
+  }
+  cudaMemcpyAsync(pts, xk, (size_t)3 * n * sizeof(float), dx ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(pts + 3 * n, yk, (size_t)3 * n * sizeof(float), dy ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+  landmark_errors(L.g, ctx->u01, pts, pts + 3 * n, n, L.hx, L.hy, L.hz, e, s);
+  cudaMemcpyAsync(err, e, (size_t)n * sizeof(double), de ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+  const cudaError_t le = cudaGetLastError();
+  rc = wait_stream(ctx);
+  cudaFree(pts);
+  cudaFree(e);
+  if (le != cudaSuccess) return fail(ctx, LDDMM_ERR_CUDA, cudaGetErrorString(le));
+  return rc;
+}
+
 int lddmm_profile_start(lddmm_ctx* ctx, int max_launches) {
   if (!ctx || max_launches < 1) return fail(ctx, LDDMM_ERR_INVALID_ARG, "bad argument");
   for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);

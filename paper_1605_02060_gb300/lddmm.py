@@ -89,6 +89,8 @@ _SIGS = {
     "lddmm_apply_K": (ctypes.c_int, [_P, _P, _P]),
     "lddmm_energy_eval": (ctypes.c_int, [_P, ctypes.POINTER(lddmm_energy)]),
     "lddmm_dice": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
+    "lddmm_surface_distance": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "lddmm_landmark_error": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "lddmm_energy_grad": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "lddmm_set_timeout": (ctypes.c_int, [_P, ctypes.c_float]),
     "lddmm_apply_K_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -307,6 +309,20 @@ class Lddmm:
         n = int(np.prod(A.shape))
         _check(load().lddmm_dice(self.ctx, _ptr(A), _ptr(B), n, ctypes.byref(d)), self.ctx)
         return d.value
+
+    def surface_distance(self, A, B):
+        """(Hausdorff, median, #surface voxels of A, of B) between two uint8 masks (§2.7)."""
+        out = (ctypes.c_double * 4)()
+        _check(load().lddmm_surface_distance(self.ctx, _ptr(A), _ptr(B), out), self.ctx)
+        return out[0], out[1], int(out[2]), int(out[3])
+
+    def landmark_error(self, xk, yk, out=None):
+        """|phi(x_k) - y_k| for float32 (n, 3) voxel coordinates (x, y, z); float64 (n,)."""
+        n = int(xk.shape[0])
+        if out is None:
+            out = np.empty(n, np.float64)
+        _check(load().lddmm_landmark_error(self.ctx, _ptr(xk), _ptr(yk), n, _ptr(out)), self.ctx)
+        return out
 
 
 def lddmm_apply_K_noalloc(src, dst, h=(1.0, 1.0, 1.0), alpha=0.02, gamma=1.0, stream=None):
