@@ -5,3 +5,4 @@ CPU-baseline leg.  The library never imports it; it shares no code with the CUDA
 """
 from . import lddmm  # noqa: F401
 from . import metrics  # noqa: F401
+from . import preprocess  # noqa: F401
