@@ -178,6 +178,28 @@ int lddmm_surface_distance(lddmm_ctx* ctx, const uint8_t* A, const uint8_t* B, d
  * or host memory; a host err is written before the call returns. */
 int lddmm_landmark_error(lddmm_ctx* ctx, const float* xk, const float* yk, int n, double* err);
 
+/* Image-LDDMM preprocessing (§2.2): the masks are applied to the images and the masked I0 is
+ * histogram-matched to the masked I1.  Each image gets a `bins`-bin histogram (the paper: 32) of
+ * its voxels with M > 0.5 over [min, max] of those voxels; `points` quantiles (the paper: 8) at
+ * k / (points + 1) are read off the cumulative counts, interpolated inside the bin that reaches
+ * the fraction.  out = the piecewise-linear map sending min to min, max to max and each quantile
+ * of I0 to the same quantile of I1 (end segments continued beyond), applied to I0 where
+ * M0 > 0.5, and 0 elsewhere.  I0, M0, I1, M1, out: n floats of device memory (out may alias
+ * I0); bins in [1, 1024], points in [0, 64].  Work is enqueued on `stream` (NULL: the legacy
+ * default stream); the call allocates a few hundred bytes of scratch and waits for the nodes
+ * (bounded) to report an empty mask as LDDMM_ERR_INVALID_ARG.  No context. */
+int lddmm_histogram_match(const float* I0, const float* M0, const float* I1, const float* M1,
+                          int64_t n, int bins, int points, float* out, void* stream);
+
+/* Mask generation (§2.2): out = [I > threshold] opened with the ball of radius r_open voxels
+ * (erosion, then dilation), then closed with the ball of radius r_close (dilation, then
+ * erosion); ball = offsets with dx^2 + dy^2 + dz^2 <= r^2; voxels beyond the grid count as
+ * background (the paper: 50 um and 125 um radii).  I: float [nz][ny][nx], out: uint8, device
+ * memory.  r_open, r_close in [0, 16] (0 skips that step).  Allocates one scratch volume for
+ * the duration of the call and waits for it (bounded).  No context. */
+int lddmm_mask_morphology(const float* I, int nx, int ny, int nz, float threshold, int r_open,
+                          int r_close, uint8_t* out, void* stream);
+
 /* Per-kernel device time, summed over the launches since lddmm_profile_start. */
 typedef struct {
   char name[32];

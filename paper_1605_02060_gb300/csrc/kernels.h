@@ -93,6 +93,24 @@ cudaError_t order_stats(const double* d, unsigned n, unsigned k1, unsigned k2, d
 cudaError_t landmark_errors(const Grid& g, const float* u01, const float* xk, const float* yk,
                             int n, float hx, float hy, float hz, double* e, cudaStream_t s);
 
+// ---- preprocessing of §2.2 (kernels_preprocess.cu) ----
+// st[0], st[1]: min and max of I over M > 0.5 (ordered-int encoding), st[2]: their count.
+cudaError_t masked_range(const float* I, const float* M, int64_t n, int* st, cudaStream_t s);
+// counts[bins]: histogram of I over M > 0.5 on [min, max] from st.
+cudaError_t masked_hist(const float* I, const float* M, int64_t n, const int* st, int bins,
+                        unsigned long long* counts, cudaStream_t s);
+// nodes: points + 2 source intensities, then points + 2 reference intensities (FP64).
+cudaError_t match_nodes(const int* st0, const unsigned long long* c0, const int* st1,
+                        const unsigned long long* c1, int bins, int points, double* nodes,
+                        cudaStream_t s);
+// out = the piecewise-linear map of I0 through the nodes where M0 > 0.5, else 0.
+cudaError_t apply_match(const float* I0, const float* M0, int64_t n, const double* nodes,
+                        int points, float* out, cudaStream_t s);
+cudaError_t threshold_mask(const float* I, int64_t n, float t, uint8_t* out, cudaStream_t s);
+// Erosion (erode) or dilation by the ball of radius r; beyond the grid is background.
+cudaError_t ball_op(const Grid& g, const uint8_t* in, int r, bool erode, uint8_t* out,
+                    cudaStream_t s);
+
 // ---- exact gradient of the discrete energy (kernels_adjoint.cu) ----
 void launch_adj_init(const Grid& g, const float* uT, const float* I0, const float* I1,
                      const float* M, float* gT, float scale, cudaStream_t s);

@@ -841,6 +841,90 @@ int lddmm_landmark_error(lddmm_ctx* ctx, const float* xk, const float* yk, int n
   return rc;
 }
 
+namespace {
+// Bounded wait for calls without a context.
+int wait_plain(cudaStream_t s, double limit = 600.0) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t e = cudaStreamQuery(s);
+    if (e == cudaSuccess) return LDDMM_OK;
+    if (e != cudaErrorNotReady)
+      return fail(nullptr, LDDMM_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > limit) return fail(nullptr, LDDMM_ERR_TIMEOUT, "timed out waiting for the GPU stream");
+    std::this_thread::sleep_for(std::chrono::microseconds(el < 0.01 ? 5 : 200));
+  }
+}
+}  // namespace
+
+int lddmm_histogram_match(const float* I0, const float* M0, const float* I1, const float* M1,
+                          int64_t n, int bins, int points, float* out, void* stream) {
+  if (!I0 || !M0 || !I1 || !M1 || !out || n <= 0 || bins < 1 || bins > 1024 || points < 0 ||
+      points > 64)
+    return fail(nullptr, LDDMM_ERR_INVALID_ARG, "bad argument");
+  const void* ps[5] = {I0, M0, I1, M1, out};
+  for (const void* p : ps)
+    if (!is_device_ptr(p)) return fail(nullptr, LDDMM_ERR_INVALID_ARG, "device memory expected");
+  cudaStream_t s = (cudaStream_t)stream;
+  // scratch: two range records (3 ints each, 16-byte slots), two histograms, the nodes
+  char* scr = nullptr;
+  const size_t hb = (size_t)bins * sizeof(unsigned long long);
+  if (cudaMalloc((void**)&scr, 32 + 2 * hb + 2 * 66 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, LDDMM_ERR_OOM, "device allocation failed");
+  }
+  int* st0 = reinterpret_cast<int*>(scr);
+  int* st1 = st0 + 4;
+  unsigned long long* c0 = reinterpret_cast<unsigned long long*>(scr + 32);
+  unsigned long long* c1 = c0 + bins;
+  double* nodes = reinterpret_cast<double*>(scr + 32 + 2 * hb);
+  int cnt[8] = {0};
+  cudaError_t e = masked_range(I0, M0, n, st0, s);
+  if (e == cudaSuccess) e = masked_range(I1, M1, n, st1, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cnt, scr, 32, cudaMemcpyDeviceToHost, s);
+  int rc = e == cudaSuccess ? wait_plain(s) : fail(nullptr, LDDMM_ERR_CUDA, cudaGetErrorString(e));
+  if (rc == LDDMM_OK && (cnt[2] == 0 || cnt[6] == 0))
+    rc = fail(nullptr, LDDMM_ERR_INVALID_ARG, "a mask is empty");
+  if (rc == LDDMM_OK) {
+    e = masked_hist(I0, M0, n, st0, bins, c0, s);
+    if (e == cudaSuccess) e = masked_hist(I1, M1, n, st1, bins, c1, s);
+    if (e == cudaSuccess) e = match_nodes(st0, c0, st1, c1, bins, points, nodes, s);
+    if (e == cudaSuccess) e = apply_match(I0, M0, n, nodes, points, out, s);
+    rc = e == cudaSuccess ? wait_plain(s) : fail(nullptr, LDDMM_ERR_CUDA, cudaGetErrorString(e));
+  }
+  cudaFree(scr);
+  return rc;
+}
+
+int lddmm_mask_morphology(const float* I, int nx, int ny, int nz, float threshold, int r_open,
+                          int r_close, uint8_t* out, void* stream) {
+  if (!I || !out || nx < 1 || ny < 1 || nz < 1 || r_open < 0 || r_open > 16 || r_close < 0 ||
+      r_close > 16)
+    return fail(nullptr, LDDMM_ERR_INVALID_ARG, "bad argument");
+  if (!is_device_ptr(I) || !is_device_ptr(out))
+    return fail(nullptr, LDDMM_ERR_INVALID_ARG, "device memory expected");
+  const Grid g{nx, ny, nz, (int64_t)nx * ny * nz};
+  cudaStream_t s = (cudaStream_t)stream;
+  uint8_t* tmp = nullptr;
+  if (cudaMalloc((void**)&tmp, (size_t)g.N) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, LDDMM_ERR_OOM, "device allocation failed");
+  }
+  // out -> tmp -> out per pair of operations
+  cudaError_t e = threshold_mask(I, g.N, threshold, out, s);
+  if (e == cudaSuccess && r_open > 0) {
+    e = ball_op(g, out, r_open, true, tmp, s);
+    if (e == cudaSuccess) e = ball_op(g, tmp, r_open, false, out, s);
+  }
+  if (e == cudaSuccess && r_close > 0) {
+    e = ball_op(g, out, r_close, false, tmp, s);
+    if (e == cudaSuccess) e = ball_op(g, tmp, r_close, true, out, s);
+  }
+  const int rc = e == cudaSuccess ? wait_plain(s) : fail(nullptr, LDDMM_ERR_CUDA, cudaGetErrorString(e));
+  cudaFree(tmp);
+  return rc;
+}
+
 int lddmm_profile_start(lddmm_ctx* ctx, int max_launches) {
   if (!ctx || max_launches < 1) return fail(ctx, LDDMM_ERR_INVALID_ARG, "bad argument");
   for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);

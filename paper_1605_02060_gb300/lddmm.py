@@ -91,6 +91,10 @@ _SIGS = {
     "lddmm_dice": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
     "lddmm_surface_distance": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "lddmm_landmark_error": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "lddmm_histogram_match": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int,
+                                             ctypes.c_int, _P, _P]),
+    "lddmm_mask_morphology": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_float, ctypes.c_int, ctypes.c_int, _P, _P]),
     "lddmm_energy_grad": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "lddmm_set_timeout": (ctypes.c_int, [_P, ctypes.c_float]),
     "lddmm_apply_K_noalloc": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -323,6 +327,41 @@ class Lddmm:
             out = np.empty(n, np.float64)
         _check(load().lddmm_landmark_error(self.ctx, _ptr(xk), _ptr(yk), n, _ptr(out)), self.ctx)
         return out
+
+
+def _current_stream():
+    """torch's current CUDA stream as a c_void_p (None when torch or CUDA is absent)."""
+    try:
+        import torch
+        if not torch.cuda.is_available():
+            return None
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        return None
+
+
+def histogram_match(I0, M0, I1, M1, out=None, bins=32, points=8):
+    """Masked I0 histogram-matched to masked I1 (§2.2), device float32 tensors of one shape."""
+    import torch
+    if out is None:
+        out = torch.empty_like(I0)
+    rc = load().lddmm_histogram_match(_ptr(I0), _ptr(M0), _ptr(I1), _ptr(M1), I0.numel(), bins,
+                                      points, _ptr(out), _current_stream())
+    _check(rc, None)
+    return out
+
+
+def mask_morphology(I, threshold, r_open, r_close, out=None):
+    """[I > threshold] opened with ball(r_open), closed with ball(r_close) (§2.2); device
+    float32 (nz, ny, nx) in, uint8 out."""
+    import torch
+    nz, ny, nx = I.shape
+    if out is None:
+        out = torch.empty(I.shape, dtype=torch.uint8, device=I.device)
+    rc = load().lddmm_mask_morphology(_ptr(I), nx, ny, nz, float(threshold), int(r_open),
+                                      int(r_close), _ptr(out), _current_stream())
+    _check(rc, None)
+    return out
 
 
 def lddmm_apply_K_noalloc(src, dst, h=(1.0, 1.0, 1.0), alpha=0.02, gamma=1.0, stream=None):
