@@ -60,6 +60,7 @@ class Params:
     T: int = 10
     epsilon: float = 1e-3
     h: tuple = (1.0, 1.0, 1.0)     # voxel spacing (hx, hy, hz)
+    integrator: str = "sl"         # "sl": one lookup per step; "rk4": RK4 along the step (§2.4)
 
 
 @dataclasses.dataclass
@@ -172,6 +173,29 @@ def _vox(vj, h):
     return np.stack([vj[0] / h[0], vj[1] / h[1], vj[2] / h[2]])
 
 
+def _step_disp(vj, p: Params, sign, grid):
+    """Displacement (voxels) of one time step along the characteristic of v_j from each grid
+    point: sign dt v_j(x) / h (semi-Lagrangian), or RK4 on dy/dt = sign v_j(y) / h over dt with
+    v_j held over the step and read at the stage points by trilinear interpolation (the paper's
+    4th-order Runge-Kutta, §2.4).  sign = +1 for phi_{j,1}, -1 for phi_{j+1,0}."""
+    gz, gy, gx = grid
+    dt = 1.0 / p.T
+    k1 = sign * dt * _vox(np.asarray(vj, np.float64), p.h)
+    if p.integrator == "sl":
+        return k1
+    if p.integrator != "rk4":
+        raise ValueError("integrator must be 'sl' or 'rk4'")
+    vjh = _vox(np.asarray(vj, np.float64), p.h)
+
+    def f(d):
+        return sign * dt * interp_vec(vjh, gx + d[0], gy + d[1], gz + d[2])
+
+    k2 = f(0.5 * k1)
+    k3 = f(0.5 * k2)
+    k4 = f(k3)
+    return (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0
+
+
 def backward_sweep(v, I1, M, p: Params):
     """phi_{j,1} for j = T-1..0, and the target-side terms J1_j = I1 o phi_{j,1},
     W_j = (M o phi_{j,1}) det D phi_{j,1}.  Returns (J1, W, u01, min_det)."""
@@ -184,7 +208,7 @@ def backward_sweep(v, I1, M, p: Params):
     W = np.empty((T,) + shape)
     min_det = np.inf
     for j in range(T - 1, -1, -1):
-        d = dt * _vox(np.asarray(v[j], np.float64), p.h)
+        d = _step_disp(v[j], p, +1.0, (gz, gy, gx))
         u = d + interp_vec(u, gx + d[0], gy + d[1], gz + d[2])
         px, py, pz = gx + u[0], gy + u[1], gz + u[2]
         det = jacobian_det(u)
@@ -209,8 +233,8 @@ def forward_sweep(v, I0, I1, M, J1, W, p: Params):
         r = c * W[j] * (J0 - J1[j])
         for e in range(3):
             b[j, e] = r * g[e] / p.h[e]
-        d = dt * _vox(np.asarray(v[j], np.float64), p.h)
-        u = -d + interp_vec(u, gx - d[0], gy - d[1], gz - d[2])
+        d = _step_disp(v[j], p, -1.0, (gz, gy, gx))
+        u = d + interp_vec(u, gx + d[0], gy + d[1], gz + d[2])
     J0T = trilinear(I0, gx + u[0], gy + u[1], gz + u[2])
     E_data = data_energy(J0T, I1, M, p)
     return b, u, J0T, E_data
@@ -240,8 +264,8 @@ def energy(v, I0, I1, M, p: Params):
     gz, gy, gx = _grid(shape)
     u = np.zeros((3,) + shape)
     for j in range(T):
-        d = dt * _vox(np.asarray(v[j], np.float64), p.h)
-        u = -d + interp_vec(u, gx - d[0], gy - d[1], gz - d[2])
+        d = _step_disp(v[j], p, -1.0, (gz, gy, gx))
+        u = d + interp_vec(u, gx + d[0], gy + d[1], gz + d[2])
     J0T = trilinear(I0, gx + u[0], gy + u[1], gz + u[2])
     return reg_energy(v, p) + data_energy(J0T, I1, M, p)
 
@@ -316,6 +340,8 @@ def _trilinear_adjoint(g, shape, qx, qy, qz):
 def energy_grad_exact(v, I0, I1, M, p: Params):
     """Euclidean gradient dE/dv of the discrete energy above, by reverse-mode differentiation
     of the forward sweep and of the stencil regulariser.  Returns (E, grad (T,3,Z,Y,X))."""
+    if p.integrator != "sl":
+        raise ValueError("the exact gradient is built for the semi-Lagrangian flow")
     v = np.asarray(v, np.float64)
     I0 = np.asarray(I0, np.float64)
     I1 = np.asarray(I1, np.float64)

@@ -353,3 +353,67 @@ def test_upsample_velocity_reproduces_affine_fields():
     ref = 0.3 * phys(fx, ff) - 0.2 * phys(fy, ff) + 0.1 * phys(fz, ff) + 1.0
     inside = (fx >= 1) & (fx <= 10) & (fy >= 1) & (fy <= 8) & (fz >= 1) & (fz <= 6)
     np.testing.assert_allclose(up[0, 0][inside], ref[inside], atol=1e-12)
+
+
+# --------------------------------------------------------------------------------------------
+# RK4 along each time step (the paper's integrator, §2.4)
+
+def _linear_velocity(A, c, shape, T):
+    Z, Y, X = shape
+    gz, gy, gx = np.meshgrid(np.arange(Z), np.arange(Y), np.arange(X), indexing="ij")
+    q = np.stack([gx - c[0], gy - c[1], gz - c[2]]).astype(np.float64)
+    v = np.einsum("ij,jzyx->izyx", A, q)
+    return np.broadcast_to(v, (T, 3) + shape).copy()
+
+
+def test_rk4_matches_the_truncated_exponential_on_a_linear_field():
+    """v(x) = A (x - c), held over each step: RK4 advances an affine map by the 4th-order Taylor
+    polynomial P of exp(A dt), and trilinear interpolation of affine displacements is exact, so
+    inside the grid phi_{0,1}(x) = c + P^T (x - c) and phi_{1,0}(x) = c + Q^T (x - c) with Q the
+    polynomial of exp(-A dt), to rounding; the one-lookup scheme is only first order."""
+    from oracle import lddmm as O
+    rng = np.random.default_rng(7)
+    A = 0.25 * rng.standard_normal((3, 3))
+    shape, T = (26, 26, 26), 4
+    c = (12.5, 12.5, 12.5)
+    v = _linear_velocity(A, c, shape, T)
+    I = np.zeros(shape)
+    p = O.Params(T=T, integrator="rk4")
+    _, _, u01, _ = O.backward_sweep(v, I, I, p)
+    _, u10, _, _ = O.forward_sweep(v, I, I, I, np.zeros((T,) + shape), np.zeros((T,) + shape), p)
+
+    def taylor(B):
+        P, term = np.eye(3), np.eye(3)
+        for k in range(1, 5):
+            term = term @ B / k
+            P = P + term
+        return P
+
+    Pf = np.linalg.matrix_power(taylor(A / T), T)
+    Pb = np.linalg.matrix_power(taylor(-A / T), T)
+    sl = O.Params(T=T)
+    _, _, u01_sl, _ = O.backward_sweep(v, I, I, sl)
+    z, y, x = np.meshgrid(*[np.arange(10, 16)] * 3, indexing="ij")
+    q = np.stack([x - c[0], y - c[1], z - c[2]]).reshape(3, -1)
+    exp_f = (Pf - np.eye(3)) @ q
+    exp_b = (Pb - np.eye(3)) @ q
+    got_f = u01[:, 10:16, 10:16, 10:16].reshape(3, -1)
+    got_b = u10[:, 10:16, 10:16, 10:16].reshape(3, -1)
+    assert np.max(np.abs(got_f - exp_f)) < 1e-10
+    assert np.max(np.abs(got_b - exp_b)) < 1e-10
+    # the exact flow differs from RK4 by O(dt^4) and from one lookup per step by O(dt)
+    from scipy.linalg import expm
+    err_rk = np.max(np.abs(got_f - (expm(A) - np.eye(3)) @ q))
+    err_sl = np.max(np.abs(u01_sl[:, 10:16, 10:16, 10:16].reshape(3, -1) - (expm(A) - np.eye(3)) @ q))
+    assert err_rk < 1e-3 < err_sl
+
+
+def test_rk4_equals_one_lookup_for_a_spatially_constant_field():
+    from oracle import lddmm as O
+    rng = np.random.default_rng(8)
+    shape, T = (10, 11, 12), 3
+    v = np.broadcast_to(rng.normal(0, 2.0, size=(T, 3, 1, 1, 1)), (T, 3) + shape).copy()
+    I1 = rng.random(shape)
+    a = O.backward_sweep(v, I1, I1, O.Params(T=T, integrator="rk4"))
+    b = O.backward_sweep(v, I1, I1, O.Params(T=T))
+    assert np.allclose(a[2], b[2], atol=1e-12) and np.allclose(a[0], b[0], atol=1e-12)
