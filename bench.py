@@ -376,6 +376,9 @@ def measure_extras(L, I0, I1, M, stream, dev):
                      ("fp32_storage_fp32_K", dict(k_mode=0))):
         p = L.default_params(X, Y, Z, T=T, **kw)
         out[name + "_iters_per_s"] = round(_time_steps(L, p, I0, I1, M, stream), 2)
+    # the paper's integrator: 4 time steps of RK4 along each characteristic (flags bit 2)
+    p = L.default_params(X, Y, Z, T=4, k_mode=1, flags=4)
+    out["rk4_T4_bf16x3_K_iters_per_s"] = round(_time_steps(L, p, I0, I1, M, stream), 2)
     pair = synth.union_pair((128, 128, 128), seed=100, amplitude=5.0)
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     for flags, name in ((0, "adjoint_128cubed_ms"), (2, "adjoint_128cubed_checkpointed_ms")):

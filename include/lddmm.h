@@ -82,7 +82,11 @@ typedef struct {
   int level_factor[4];       /* coarse -> fine downsampling factors, last must be 1, e.g. 4,2,1 */
   int k_mode;                /* LDDMM_K_*                                                    */
   int flags;                 /* bit 0: halve epsilon and retry when the energy increases;
-                                bit 1: checkpoint the forward maps in lddmm_energy_grad       */
+                                bit 1: checkpoint the forward maps in lddmm_energy_grad;
+                                bit 2: integrate each time step by RK4 along the characteristic
+                                (v_j held over the step, read by trilinear lookups at the
+                                stages; the paper's integrator, §2.4) instead of one lookup.
+                                lddmm_energy_grad rejects bit 2.                             */
   float timeout_s;           /* bound on every host wait for the stream (<= 0: 600 s)        */
   int storage;               /* 0: v and images stored float32; 1: stored bf16 (FP32 arithmetic,
                                 FP64 reductions; the precision form)                          */

@@ -39,7 +39,7 @@ enum KernelId {
 // interleaved as pairs (launch_interleave).
 void launch_flow_back(const Grid& g, const void* vj, const float* u_next, float* u_cur,
                       const void* IM, float* J1j, float* Wj, float dtx, float dty, float dtz,
-                      Acc* acc, cudaStream_t s, const Hook& hook, int st);
+                      Acc* acc, cudaStream_t s, const Hook& hook, int st, int rk = 0);
 // out[i] = (a[i], b[i]) as storage-type pairs.
 void launch_interleave(const void* a, const void* b, void* out, int64_t n, cudaStream_t s,
                        int st);
@@ -53,17 +53,18 @@ void launch_fwd_terms(const Grid& g, const float* u_cur, const void* I0, const f
 // if last, J0_T = I0 o (id + u_next) and E_data.
 void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u_next,
                      float dtx, float dty, float dtz, bool last, const void* I0, const void* I1,
-                     const void* M, float* J0T, Acc* acc, cudaStream_t s, int st);
+                     const void* M, float* J0T, Acc* acc, cudaStream_t s, int st, int rk = 0);
 // E_reg of all T fields v[T][3][N] into acc->e_reg (unscaled sum of |(gamma - alpha Lap_h) v|^2).
 void launch_ereg(const Grid& g, const void* v, int T, float alpha, float gamma, float ihx2,
                  float ihy2, float ihz2, Acc* acc, cudaStream_t s, int st);
 // v_j <- v_j - eps (2 v_j - Kb), 3 components.
 void launch_update(const Grid& g, void* vj, const float* Kb, float eps, cudaStream_t s, int st);
 // Displacement of phi_{1,0} / phi_{0,1} only (flows without the residual), to refresh maps.
+// rk = 1: RK4 along each step (v_j held over the step) instead of one lookup.
 void launch_flow_only_fwd(const Grid& g, const void* vj, const float* u_cur, float* u_next,
-                          float dtx, float dty, float dtz, cudaStream_t s, int st);
+                          float dtx, float dty, float dtz, cudaStream_t s, int st, int rk = 0);
 void launch_flow_only_back(const Grid& g, const void* vj, const float* u_next, float* u_cur,
-                           float dtx, float dty, float dtz, cudaStream_t s, int st);
+                           float dtx, float dty, float dtz, cudaStream_t s, int st, int rk = 0);
 void launch_warp(const Grid& g, const float* src, const float* u, float* dst, cudaStream_t s);
 void launch_labels(const Grid& g, const uint16_t* L0, const float* u, uint16_t* dst,
                    cudaStream_t s);

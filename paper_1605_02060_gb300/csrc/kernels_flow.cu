@@ -35,7 +35,31 @@ static const dim3 kBlock3d(32, 8, 1);
 // costs two dependent memory latencies (v_j, then the eight corners at the displaced point); the
 // velocity of plane z+1 is loaded before the corners of plane z are requested, so the two
 // overlap.  Consecutive planes also gather from overlapping cells, which L1 keeps.
-template <typename ST, int SGN, int ZC>
+// RK4 displacement (voxels) of one time step of dy/dt = s v_j(y) / h from the grid point
+// (x, y, z), v_j held over the step (the paper's 4th-order Runge-Kutta, §2.4): k1 from the grid
+// value (a0, a1, a2), k2, k3, k4 from trilinear lookups of v_j at the stage points;
+// c = s dt / h per axis.
+template <typename ST>
+__device__ __forceinline__ void rk4_disp(const Grid& g, const ST* __restrict__ vj, float x,
+                                         float y, float z, float a0, float a1, float a2,
+                                         float cx, float cy, float cz, float& d0, float& d1,
+                                         float& d2) {
+  const float k1x = cx * a0, k1y = cy * a1, k1z = cz * a2;
+  Tri w = tri_setup(g, x + 0.5f * k1x, y + 0.5f * k1y, z + 0.5f * k1z);
+  const float k2x = cx * tri_apply_t(vj, w), k2y = cy * tri_apply_t(vj + g.N, w),
+              k2z = cz * tri_apply_t(vj + 2 * g.N, w);
+  w = tri_setup(g, x + 0.5f * k2x, y + 0.5f * k2y, z + 0.5f * k2z);
+  const float k3x = cx * tri_apply_t(vj, w), k3y = cy * tri_apply_t(vj + g.N, w),
+              k3z = cz * tri_apply_t(vj + 2 * g.N, w);
+  w = tri_setup(g, x + k3x, y + k3y, z + k3z);
+  const float k4x = cx * tri_apply_t(vj, w), k4y = cy * tri_apply_t(vj + g.N, w),
+              k4z = cz * tri_apply_t(vj + 2 * g.N, w);
+  d0 = (k1x + 2.f * k2x + 2.f * k3x + k4x) / 6.f;
+  d1 = (k1y + 2.f * k2y + 2.f * k3y + k4y) / 6.f;
+  d2 = (k1z + 2.f * k2z + 2.f * k3z + k4z) / 6.f;
+}
+
+template <typename ST, int SGN, int ZC, bool RK>
 __global__ void __launch_bounds__(256) k_disp_march(Grid g, const ST* __restrict__ vj,
                                                     const float* __restrict__ uin,
                                                     float* __restrict__ uout, float dtx,
@@ -53,8 +77,15 @@ __global__ void __launch_bounds__(256) k_disp_march(Grid g, const ST* __restrict
       n1 = ldf_now(vj + g.N + idx + plane);
       n2 = ldf_now(vj + 2 * g.N + idx + plane);
     }
-    const float dx = (float)SGN * (dtx * a0), dy = (float)SGN * (dty * a1),
-                dz = (float)SGN * (dtz * a2);
+    float dx, dy, dz;
+    if (RK) {
+      rk4_disp(g, vj, (float)x, (float)y, (float)z, a0, a1, a2, (float)SGN * dtx,
+               (float)SGN * dty, (float)SGN * dtz, dx, dy, dz);
+    } else {
+      dx = (float)SGN * (dtx * a0);
+      dy = (float)SGN * (dty * a1);
+      dz = (float)SGN * (dtz * a2);
+    }
     float ox = dx, oy = dy, oz = dz;
     if (uin) {
       const Tri w = tri_setup(g, (float)x + dx, (float)y + dy, (float)z + dz);
@@ -77,20 +108,24 @@ constexpr int kFlowZ = 4;
 
 template <typename ST, int SGN>
 static void launch_disp_march(const Grid& g, const void* vj, const float* uin, float* uout,
-                              float dtx, float dty, float dtz, cudaStream_t s) {
+                              float dtx, float dty, float dtz, cudaStream_t s, int rk) {
   const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + kFlowZ - 1) / kFlowZ);
-  k_disp_march<ST, SGN, kFlowZ><<<grid, kBlock3d, 0, s>>>(g, (const ST*)vj, uin, uout, dtx, dty,
-                                                          dtz);
+  if (rk)
+    k_disp_march<ST, SGN, kFlowZ, true><<<grid, kBlock3d, 0, s>>>(g, (const ST*)vj, uin, uout,
+                                                                  dtx, dty, dtz);
+  else
+    k_disp_march<ST, SGN, kFlowZ, false><<<grid, kBlock3d, 0, s>>>(g, (const ST*)vj, uin, uout,
+                                                                   dtx, dty, dtz);
 }
 
 static void disp_step(int sgn, const Grid& g, const void* vj, const float* uin, float* uout,
-                      float dtx, float dty, float dtz, cudaStream_t s, int st) {
+                      float dtx, float dty, float dtz, cudaStream_t s, int st, int rk) {
   if (sgn > 0) {
-    if (st) launch_disp_march<__nv_bfloat16, 1>(g, vj, uin, uout, dtx, dty, dtz, s);
-    else launch_disp_march<float, 1>(g, vj, uin, uout, dtx, dty, dtz, s);
+    if (st) launch_disp_march<__nv_bfloat16, 1>(g, vj, uin, uout, dtx, dty, dtz, s, rk);
+    else launch_disp_march<float, 1>(g, vj, uin, uout, dtx, dty, dtz, s, rk);
   } else {
-    if (st) launch_disp_march<__nv_bfloat16, -1>(g, vj, uin, uout, dtx, dty, dtz, s);
-    else launch_disp_march<float, -1>(g, vj, uin, uout, dtx, dty, dtz, s);
+    if (st) launch_disp_march<__nv_bfloat16, -1>(g, vj, uin, uout, dtx, dty, dtz, s, rk);
+    else launch_disp_march<float, -1>(g, vj, uin, uout, dtx, dty, dtz, s, rk);
   }
 }
 
@@ -217,9 +252,9 @@ void launch_interleave(const void* a, const void* b, void* out, int64_t n, cudaS
 
 void launch_flow_back(const Grid& g, const void* vj, const float* u_next, float* u_cur,
                       const void* IM, float* J1j, float* Wj, float dtx, float dty, float dtz,
-                      Acc* acc, cudaStream_t s, const Hook& hook, int st) {
+                      Acc* acc, cudaStream_t s, const Hook& hook, int st, int rk) {
   hook(KID_BACK_DISP, 0);
-  disp_step(+1, g, vj, u_next, u_cur, dtx, dty, dtz, s, st);
+  disp_step(+1, g, vj, u_next, u_cur, dtx, dty, dtz, s, st, rk);
   hook(KID_BACK_DISP, 1);
   hook(KID_BACK_TERMS, 0);
   const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + kFlowZ - 1) / kFlowZ);
@@ -233,8 +268,8 @@ void launch_flow_back(const Grid& g, const void* vj, const float* u_next, float*
 }
 
 void launch_flow_only_back(const Grid& g, const void* vj, const float* u_next, float* u_cur,
-                           float dtx, float dty, float dtz, cudaStream_t s, int st) {
-  disp_step(+1, g, vj, u_next, u_cur, dtx, dty, dtz, s, st);
+                           float dtx, float dty, float dtz, cudaStream_t s, int st, int rk) {
+  disp_step(+1, g, vj, u_next, u_cur, dtx, dty, dtz, s, st, rk);
 }
 
 // --------------------------------------------------------------------------------------------
@@ -337,7 +372,7 @@ void launch_fwd_terms(const Grid& g, const float* u_cur, const void* I0, const f
 // (the velocity of plane z+1 is loaded before plane z's lookups), so the three dependent
 // latencies of a voxel (v, the map at the displaced point, I0 at the mapped point) overlap with
 // the next plane's.
-template <typename ST, int ZC>
+template <typename ST, int ZC, bool RK>
 __global__ void __launch_bounds__(256) k_fwd_last_march(Grid g, const ST* __restrict__ vj,
                                                         const float* __restrict__ uc,
                                                         float* __restrict__ un, float dtx,
@@ -360,10 +395,17 @@ __global__ void __launch_bounds__(256) k_fwd_last_march(Grid g, const ST* __rest
         n1 = ldf_now(vj + g.N + idx + plane);
         n2 = ldf_now(vj + 2 * g.N + idx + plane);
       }
-      const float dx = dtx * a0, dy = dty * a1, dz = dtz * a2;
-      float ox = -dx, oy = -dy, oz = -dz;
+      float dx, dy, dz;       // the step's displacement (voxels), backward in time
+      if (RK) {
+        rk4_disp(g, vj, (float)x, (float)y, (float)z, a0, a1, a2, -dtx, -dty, -dtz, dx, dy, dz);
+      } else {
+        dx = -(dtx * a0);
+        dy = -(dty * a1);
+        dz = -(dtz * a2);
+      }
+      float ox = dx, oy = dy, oz = dz;
       if (uc) {
-        const Tri w = tri_setup(g, (float)x - dx, (float)y - dy, (float)z - dz);
+        const Tri w = tri_setup(g, (float)x + dx, (float)y + dy, (float)z + dz);
         ox += tri_apply(uc, w);
         oy += tri_apply(uc + g.N, w);
         oz += tri_apply(uc + 2 * g.N, w);
@@ -385,20 +427,24 @@ __global__ void __launch_bounds__(256) k_fwd_last_march(Grid g, const ST* __rest
 
 void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u_next,
                      float dtx, float dty, float dtz, bool last, const void* I0, const void* I1,
-                     const void* M, float* J0T, Acc* acc, cudaStream_t s, int st) {
+                     const void* M, float* J0T, Acc* acc, cudaStream_t s, int st, int rk) {
   if (!last) {
-    disp_step(-1, g, vj, u_cur, u_next, dtx, dty, dtz, s, st);
+    disp_step(-1, g, vj, u_cur, u_next, dtx, dty, dtz, s, st, rk);
     return;
   }
   const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + kFlowZ - 1) / kFlowZ);
-  if (st)
-    k_fwd_last_march<__nv_bfloat16, kFlowZ><<<grid, kBlock3d, 0, s>>>(
-        g, (const __nv_bfloat16*)vj, u_cur, u_next, dtx, dty, dtz, (const __nv_bfloat16*)I0,
-        (const __nv_bfloat16*)I1, (const __nv_bfloat16*)M, J0T, acc);
-  else
-    k_fwd_last_march<float, kFlowZ><<<grid, kBlock3d, 0, s>>>(
-        g, (const float*)vj, u_cur, u_next, dtx, dty, dtz, (const float*)I0, (const float*)I1,
-        (const float*)M, J0T, acc);
+#define FWD_LAST(ST_, RK_)                                                                    \
+  k_fwd_last_march<ST_, kFlowZ, RK_><<<grid, kBlock3d, 0, s>>>(                               \
+      g, (const ST_*)vj, u_cur, u_next, dtx, dty, dtz, (const ST_*)I0, (const ST_*)I1,       \
+      (const ST_*)M, J0T, acc)
+  if (st) {
+    if (rk) FWD_LAST(__nv_bfloat16, true);
+    else FWD_LAST(__nv_bfloat16, false);
+  } else {
+    if (rk) FWD_LAST(float, true);
+    else FWD_LAST(float, false);
+  }
+#undef FWD_LAST
 }
 
 // --------------------------------------------------------------------------------------------
@@ -548,8 +594,8 @@ void launch_ereg(const Grid& g, const void* v, int T, float alpha, float gamma, 
 }
 
 void launch_flow_only_fwd(const Grid& g, const void* vj, const float* u_cur, float* u_next,
-                          float dtx, float dty, float dtz, cudaStream_t s, int st) {
-  disp_step(-1, g, vj, u_cur, u_next, dtx, dty, dtz, s, st);
+                          float dtx, float dty, float dtz, cudaStream_t s, int st, int rk) {
+  disp_step(-1, g, vj, u_cur, u_next, dtx, dty, dtz, s, st, rk);
 }
 
 // --------------------------------------------------------------------------------------------

@@ -175,7 +175,7 @@ int validate(const lddmm_params* p, std::string& why) {
   if (p->k_mode != LDDMM_K_FP32 && (p->nx > 512 || p->ny > 512 || p->nz > 512)) {
     why = "tensor-core K needs every axis <= 512 (TMEM columns)"; return LDDMM_ERR_INVALID_ARG;
   }
-  if (p->flags & ~3) { why = "unknown flag bits"; return LDDMM_ERR_INVALID_ARG; }
+  if (p->flags & ~7) { why = "unknown flag bits"; return LDDMM_ERR_INVALID_ARG; }
   if (p->storage != 0 && p->storage != 1) { why = "storage must be 0 (float) or 1 (bf16)"; return LDDMM_ERR_INVALID_ARG; }
   return LDDMM_OK;
 }
@@ -258,6 +258,9 @@ void release(lddmm_ctx* ctx) {
 
 inline float dtv(const lddmm_ctx* ctx, float h) { return 1.0f / (float)ctx->p.T / h; }
 
+// flags bit 2: RK4 along each time step instead of one lookup
+inline int rk_of(const lddmm_ctx* ctx) { return (ctx->p.flags >> 2) & 1; }
+
 // v_j in the storage type (3 components of N elements each)
 inline void* vptr(const lddmm_ctx* ctx, int j, int64_t N) {
   return reinterpret_cast<char*>(ctx->v) + (size_t)j * 3 * N * ctx->es;
@@ -317,7 +320,7 @@ int run_step(lddmm_ctx* ctx) {
   for (int j = T - 1; j >= 0; --j) {
     float* uc = ctx->uB[pb];
     launch_flow_back(g, vptr(ctx, j, N), un, uc, L.IM, ctx->J1 + j * N, ctx->W + j * N, dtx,
-                     dty, dtz, ctx->acc, s, hk, ctx->st);
+                     dty, dtz, ctx->acc, s, hk, ctx->st, rk_of(ctx));
     un = uc;
     pb ^= 1;
   }
@@ -343,7 +346,7 @@ int run_step(lddmm_ctx* ctx) {
     float* unx = ctx->uF[pf];
     hk(KID_FWD_FLOW, 0);
     launch_fwd_flow(g, vj, uc, unx, dtx, dty, dtz, j == T - 1, L.I0, L.I1, L.M, ctx->J0T,
-                    ctx->acc, s, ctx->st);
+                    ctx->acc, s, ctx->st, rk_of(ctx));
     hk(KID_FWD_FLOW, 1);
     // K b_j and the update v_j <- v_j - eps (2 v_j - K b_j): fused into the last DFT pass for
     // float storage, a separate pass for bf16 storage
@@ -382,7 +385,7 @@ int refresh_maps(lddmm_ctx* ctx, bool energy) {
   int pb = 0;
   for (int j = T - 1; j >= 0; --j) {
     float* uc = ctx->uB[pb];
-    launch_flow_only_back(g, vptr(ctx, j, N), un, uc, dtx, dty, dtz, s, ctx->st);
+    launch_flow_only_back(g, vptr(ctx, j, N), un, uc, dtx, dty, dtz, s, ctx->st, rk_of(ctx));
     un = uc;
     pb ^= 1;
   }
@@ -394,7 +397,7 @@ int refresh_maps(lddmm_ctx* ctx, bool energy) {
   for (int j = 0; j < T; ++j) {
     float* unx = ctx->uF[pf];
     launch_fwd_flow(g, vptr(ctx, j, N), uc, unx, dtx, dty, dtz, j == T - 1, L.I0, L.I1, L.M,
-                    ctx->J0T, ctx->acc, s, ctx->st);
+                    ctx->J0T, ctx->acc, s, ctx->st, rk_of(ctx));
     uc = unx;
     pf ^= 1;
   }
@@ -972,6 +975,8 @@ int lddmm_profile_stop(lddmm_ctx* ctx, lddmm_kernel_stat* out, int max_out, int*
 int lddmm_energy_grad(lddmm_ctx* ctx, const float* v, float* grad, double* E) {
   if (!ctx || !grad) return fail(ctx, LDDMM_ERR_INVALID_ARG, "NULL argument");
   if (ctx->st != 0) return fail(ctx, LDDMM_ERR_INVALID_ARG, "the exact gradient needs float storage");
+  if (rk_of(ctx))
+    return fail(ctx, LDDMM_ERR_INVALID_ARG, "the exact gradient is built for the one-lookup flow");
   const Level& L = ctx->levels[ctx->cur];
   const Grid& g = L.g;
   const int T = ctx->p.T;

@@ -48,7 +48,7 @@ def test_library_targets_sm_103a():
 
 @pytest.mark.parametrize("field,value", [("nx", 1), ("T", 0), ("sigma", 0.0), ("epsilon", -1.0),
                                          ("gamma", 0.0), ("num_levels", 5), ("k_mode", 7),
-                                         ("flags", 4), ("hx", 0.0)])
+                                         ("flags", 8), ("hx", 0.0)])
 def test_invalid_params_rejected_without_gpu(lib, field, value):
     from paper_1605_02060_gb300 import lddmm as L
     p = L.default_params(8, 8, 8)

@@ -174,6 +174,39 @@ def test_one_step_matches_oracle(L, O, synth, mode, shape, T, h):
     assert _rel(v1 - v0, ref.v_new - v0) < 1e-4
 
 
+@pytest.mark.parametrize("shape,T,h", [((32, 32, 32), 4, (1, 1, 1)),
+                                       ((20, 17, 23), 3, (1.0, 1.25, 0.8)),
+                                       ((8, 10, 260), 4, (1, 1, 1))])
+def test_one_step_rk4_matches_oracle(L, O, synth, shape, T, h):
+    """flags bit 2: RK4 along each time step (the paper's integrator); the maps, the deformed
+    template, the energies and the update against the oracle run with integrator='rk4'."""
+    Z, Y, X = shape
+    pair = synth.ellipsoid_pair(shape=shape, centre=((X - 1) / 2, (Y - 1) / 2, (Z - 1) / 2),
+                                semi_axes=(X / 3.2, Y / 4.0, Z / 4.5), width=X / 5.0,
+                                amplitude=2.0, seed=3)
+    v0 = synth.smooth_velocity(T, shape, 3.0, seed=5)
+    p = L.default_params(X, Y, Z, T=T, hx=h[0], hy=h[1], hz=h[2], k_mode=PROD, flags=4)
+    po = O.Params(T=T, h=h, integrator="rk4")
+    ref = O.lddmm_step(v0, pair.I0, pair.I1, pair.M, po)
+    sl = O.lddmm_step(v0, pair.I0, pair.I1, pair.M, O.Params(T=T, h=h))
+    with L.Lddmm(p, _dev(pair.I0), _dev(pair.I1), _dev(pair.M)) as ctx:
+        ctx.set_velocity(_dev(v0))
+        u10 = ctx.get_field(L.LDDMM_FIELD_U10)
+        u01 = ctx.get_field(L.LDDMM_FIELD_U01)
+        J0 = ctx.get_field(L.LDDMM_FIELD_J0)
+        e = ctx.step()
+        v1 = ctx.get_velocity()
+        with pytest.raises(L.LddmmError) as ei:
+            ctx.energy_grad(None, torch.empty((T, 3) + shape, device="cuda"))
+        assert ei.value.code == L.LDDMM_ERR_INVALID_ARG
+    assert _rel(u10, ref.u10) < 1e-5 and _rel(u01, ref.u01) < 1e-5
+    assert _rel(u10, sl.u10) > 1e-4          # the integrators differ at this velocity
+    assert _rel(J0, ref.J0T) < 1e-5
+    assert _rel(v1 - v0, ref.v_new - v0) < 1e-4
+    assert abs(e["reg"] - ref.E_reg) <= 1e-5 * ref.E_reg
+    assert abs(e["data"] - ref.E_data) <= 1e-5 * ref.E_data
+
+
 def test_twenty_iterations_config1(L, O, synth):
     pair = _pair_small(synth)
     T = 10
