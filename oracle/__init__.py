@@ -6,3 +6,4 @@ CPU-baseline leg.  The library never imports it; it shares no code with the CUDA
 from . import lddmm  # noqa: F401
 from . import metrics  # noqa: F401
 from . import preprocess  # noqa: F401
+from . import shooting  # noqa: F401
