@@ -412,6 +412,18 @@ def measure_extras(L, I0, I1, M, stream, dev):
     hd0, md0, _, _ = ctx.surface_distance(A0, B)
     hd, md, na, nb = ctx.surface_distance(A, B)
     dt = (time.perf_counter() - t0) / 2
+    # geodesic shooting (EPDiff, transport form) from the v_0 reached after those 20 iterations:
+    # T-1 flow steps, transports and K applications (wall time of the C call, host waits)
+    vd = torch.empty((T, 3) + tuple(SHAPE), device=dev)
+    ctx.get_velocity(vd)
+    v0 = vd[0].clone()
+    del vd
+    ctx.shoot(v0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.shoot(v0)
+    torch.cuda.synchronize()
+    out["shoot_T10_ms"] = round(1000 * (time.perf_counter() - t0), 2)
     ctx.close()
     # §2.2 preprocessing at the benchmark's grid: target mask from the target intensities
     # (threshold, ball opening r = 1, closing r = 3) and the atlas image histogram-matched to the

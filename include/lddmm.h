@@ -182,6 +182,15 @@ int lddmm_surface_distance(lddmm_ctx* ctx, const uint8_t* A, const uint8_t* B, d
  * or host memory; a host err is written before the call returns. */
 int lddmm_landmark_error(lddmm_ctx* ctx, const float* xk, const float* yk, int n, double* err);
 
+/* Geodesic shooting (EPDiff; LDDMM's minimisers are geodesics, Beg et al. 2005 cited in §2.4;
+ * the paper has no shooting step): replaces the context's v_j, j = 0..T-1, by the geodesic from
+ * v0.  The momentum m_0 = L^T L v0 is transported by the flow, m_j = |D phi| (D phi)^T (m_0 o phi)
+ * with phi = phi_{j,0} from the same semi-Lagrangian steps as the forward sweep, and
+ * v_j = K m_j with the context's K.  v0: float [3][nz][ny][nx] of the current level, device or
+ * host memory, in physical units.  Needs float storage (params.storage = 0) and the one-lookup
+ * flow (flags bit 2 clear). */
+int lddmm_shoot(lddmm_ctx* ctx, const float* v0);
+
 /* Image-LDDMM preprocessing (§2.2): the masks are applied to the images and the masked I0 is
  * histogram-matched to the masked I1.  Each image gets a `bins`-bin histogram (the paper: 32) of
  * its voxels with M > 0.5 over [min, max] of those voxels; `points` quantiles (the paper: 8) at

@@ -112,6 +112,11 @@ cudaError_t threshold_mask(const float* I, int64_t n, float t, uint8_t* out, cud
 cudaError_t ball_op(const Grid& g, const uint8_t* in, int r, bool erode, uint8_t* out,
                     cudaStream_t s);
 
+// ---- geodesic shooting (kernels_shoot.cu) ----
+// m = |D phi| (D phi)^T (m0 o phi), phi = id + u (u in voxels), 3 components of N each.
+cudaError_t transport_momentum(const Grid& g, const float* m0, const float* u, float hx,
+                               float hy, float hz, float* m, cudaStream_t s);
+
 // ---- exact gradient of the discrete energy (kernels_adjoint.cu) ----
 void launch_adj_init(const Grid& g, const float* uT, const float* I0, const float* I1,
                      const float* M, float* gT, float scale, cudaStream_t s);

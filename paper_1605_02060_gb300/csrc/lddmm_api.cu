@@ -816,6 +816,45 @@ int lddmm_surface_distance(lddmm_ctx* ctx, const uint8_t* A, const uint8_t* B, d
   return done(LDDMM_OK);
 }
 
+int lddmm_shoot(lddmm_ctx* ctx, const float* v0) {
+  if (!ctx || !v0) return fail(ctx, LDDMM_ERR_INVALID_ARG, "NULL argument");
+  if (ctx->st != 0) return fail(ctx, LDDMM_ERR_INVALID_ARG, "shooting needs float storage");
+  if (rk_of(ctx)) return fail(ctx, LDDMM_ERR_INVALID_ARG, "shooting uses the one-lookup flow");
+  const Level& L = ctx->levels[ctx->cur];
+  const Grid& g = L.g;
+  const int T = ctx->p.T;
+  const int64_t N = g.N, F = 3 * N;
+  cudaStream_t s = ctx->stream;
+  const float dtx = dtv(ctx, L.hx), dty = dtv(ctx, L.hy), dtz = dtv(ctx, L.hz);
+  const float ihx2 = 1.0f / (L.hx * L.hx), ihy2 = 1.0f / (L.hy * L.hy), ihz2 = 1.0f / (L.hz * L.hz);
+  float* v = reinterpret_cast<float*>(ctx->v);
+  CK(cudaMemcpyAsync(v, v0, F * sizeof(float), cudaMemcpyDefault, s));
+  int rc;
+  if ((rc = check_finite(ctx, v, F, "v0"))) return rc;
+  // m_0 = L (L v_0) in stage
+  launch_apply_L3(g, v, ctx->work, ctx->p.alpha, ctx->p.gamma, ihx2, ihy2, ihz2, 1.0f, false, s);
+  launch_apply_L3(g, ctx->work, ctx->stage, ctx->p.alpha, ctx->p.gamma, ihx2, ihy2, ihz2, 1.0f,
+                  false, s);
+  const float* uc = nullptr;
+  int pf = 0;
+  for (int j = 0; j + 1 < T; ++j) {
+    float* un = ctx->uF[pf];
+    launch_flow_only_fwd(g, v + (int64_t)j * F, uc, un, dtx, dty, dtz, s, 0, 0);
+    CK(transport_momentum(g, ctx->stage, un, L.hx, L.hy, L.hz, ctx->b, s));
+    CK(apply_K(L.kp, ctx->p.k_mode, ctx->b, ctx->b, ctx->work, 3, s, Hook(), nullptr, 0.f,
+               ctx->kcap));
+    CK(cudaMemcpyAsync(v + (int64_t)(j + 1) * F, ctx->b, F * sizeof(float),
+                       cudaMemcpyDeviceToDevice, s));
+    uc = un;
+    pf ^= 1;
+  }
+  CK(cudaGetLastError());
+  ctx->maps_valid = false;
+  ctx->j0_valid = false;
+  ctx->last_E = -1.0;
+  return LDDMM_OK;
+}
+
 int lddmm_landmark_error(lddmm_ctx* ctx, const float* xk, const float* yk, int n, double* err) {
   if (!ctx || !xk || !yk || !err || n < 0) return fail(ctx, LDDMM_ERR_INVALID_ARG, "bad argument");
   if (n == 0) return LDDMM_OK;

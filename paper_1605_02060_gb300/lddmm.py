@@ -91,6 +91,7 @@ _SIGS = {
     "lddmm_dice": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
     "lddmm_surface_distance": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "lddmm_landmark_error": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "lddmm_shoot": (ctypes.c_int, [_P, _P]),
     "lddmm_histogram_match": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int,
                                              ctypes.c_int, _P, _P]),
     "lddmm_mask_morphology": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -313,6 +314,10 @@ class Lddmm:
         n = int(np.prod(A.shape))
         _check(load().lddmm_dice(self.ctx, _ptr(A), _ptr(B), n, ctypes.byref(d)), self.ctx)
         return d.value
+
+    def shoot(self, v0):
+        """Replace v_j (j = 0..T-1) by the geodesic from v0, float32 (3, nz, ny, nx)."""
+        _check(load().lddmm_shoot(self.ctx, _ptr(v0)), self.ctx)
 
     def surface_distance(self, A, B):
         """(Hausdorff, median, #surface voxels of A, of B) between two uint8 masks (§2.7)."""
