@@ -473,12 +473,17 @@ def measure_warm_start():
         _, E, _, _ = SG.run_plain(pr, iters, T, flags=1)
         it_p, wall_p, dice_p = SG.run_plain_timed(pr, E[-1], 2 * iters, T, flags=1)
         it_w, c, _, wall_w = SG.run_warm(net, pr, E[-1], 2 * iters, T, flags=1)
+        e_w = SG.run_warm.last_start_energy
+        # the geodesic variant: only the prediction's v_0, with v_1..v_{T-1} shot from it
+        it_s, _, _, wall_s = SG.run_warm(net, pr, E[-1], 2 * iters, T, flags=1, shoot=True)
+        e_s = SG.run_warm.last_start_energy
         # time to the plain method's Dice: the fewest warm iterations that match it (found
         # untimed), then a timed run of exactly that many
         kd = SG.warm_iters_to_dice(net, pr, dice_p, 2 * iters, T, flags=1)
         wall_d = SG.run_warm_fixed(net, pr, kd, T, flags=1) if kd is not None else float("nan")
         rows.append((it_p, wall_p, dice_p, it_w, wall_w, SG.run_warm.last_dice,
-                     SG.warm_start_dice(net, pr, T), -1 if kd is None else kd, wall_d))
+                     SG.warm_start_dice(net, pr, T), -1 if kd is None else kd, wall_d,
+                     it_s, wall_s, e_w, e_s, E[0]))
     a = np.array(rows, dtype=np.float64)
     okd = a[:, 7] >= 0
     return {"grid": "32^3", "T": T, "train_pairs": 240, "mirror_images": 8, "epochs": 6,
@@ -495,7 +500,13 @@ def measure_warm_start():
             "dice_surrogate_only": round(a[:, 6].mean(), 4),
             "warm_iters_to_plain_dice": a[:, 7].astype(int).tolist(),
             "warm_to_dice_wall_ms_mean": round(1e3 * float(np.nanmean(a[okd, 8])), 1) if okd.any() else None,
-            "dice_wall_speedup": round(float(a[okd, 1].sum() / a[okd, 8].sum()), 3) if okd.all() else None}
+            "dice_wall_speedup": round(float(a[okd, 1].sum() / a[okd, 8].sum()), 3) if okd.all() else None,
+            "shot_iters_to_energy": a[:, 9].astype(int).tolist(),
+            "shot_wall_ms_mean": round(1e3 * a[:, 10].mean(), 1),
+            "shot_wall_speedup_median": round(float(np.median(a[:, 1] / a[:, 10])), 2),
+            "start_energy_rel_plain_start": {
+                "predicted_field": [round(float(x), 3) for x in a[:, 11] / a[:, 13]],
+                "shot_from_predicted_v0": [round(float(x), 3) for x in a[:, 12] / a[:, 13]]}}
 
 
 def ctypes_sizeof_energy():

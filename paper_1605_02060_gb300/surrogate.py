@@ -340,9 +340,24 @@ def choose_start(ctx, v_pred, scales=(0.0, 0.5, 1.0, 1.5, 2.0, 3.0)):
     return best[0], best[1], len(scales)
 
 
-def run_warm(net, pair, target_energy, max_iters, T=10, k_mode=1, flags=0):
-    """Warm start (choose_start on the prediction), then plain LDDMM until the energy reaches
-    target_energy.  Returns (iterations, chosen scale, energy evaluations, wall seconds)."""
+def choose_start_shot(ctx, v0, scales=(0.0, 0.5, 1.0, 1.5, 2.0, 3.0)):
+    """The geodesic variant of choose_start: only the initial velocity c * v0 is kept, and the
+    context's v_1..v_{T-1} are shot from it (EPDiff); the scale of lowest energy is set.
+    Returns (c, energy, energy evaluations)."""
+    best = None
+    for c in scales:
+        ctx.shoot(np.ascontiguousarray(v0 * np.float32(c)))
+        e = ctx.energy()["total"]
+        if best is None or e < best[1]:
+            best = (c, e)
+    ctx.shoot(np.ascontiguousarray(v0 * np.float32(best[0])))
+    return best[0], best[1], len(scales)
+
+
+def run_warm(net, pair, target_energy, max_iters, T=10, k_mode=1, flags=0, shoot=False):
+    """Warm start (choose_start on the prediction; with shoot=True, choose_start_shot on its
+    v_0), then plain LDDMM until the energy reaches target_energy.  Returns (iterations, chosen
+    scale, energy evaluations, wall seconds)."""
     n = pair.I0.shape
     p = L.default_params(n[2], n[1], n[0], T=T, k_mode=k_mode, flags=flags)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -350,7 +365,8 @@ def run_warm(net, pair, target_energy, max_iters, T=10, k_mode=1, flags=0):
     t0 = time.perf_counter()
     with L.Lddmm(p, dev(pair.I0), dev(pair.I1), dev(pair.M)) as ctx:
         v = smooth_prediction(ctx, warm_start_field(net, pair, T), p.gamma)
-        c, e, nev = choose_start(ctx, v)
+        c, e, nev = choose_start_shot(ctx, v[0]) if shoot else choose_start(ctx, v)
+        run_warm.last_start_energy = e
         it = 0
         while it < max_iters and e > target_energy:
             e = ctx.step()["total"]
