@@ -207,6 +207,57 @@ def test_one_step_rk4_matches_oracle(L, O, synth, shape, T, h):
     assert abs(e["data"] - ref.E_data) <= 1e-5 * ref.E_data
 
 
+def _pair_centred(synth, shape):
+    Z, Y, X = shape
+    return synth.ellipsoid_pair(shape=shape, centre=((X - 1) / 2, (Y - 1) / 2, (Z - 1) / 2),
+                                semi_axes=(X / 3.2, Y / 4.0, Z / 4.5), width=X / 5.0,
+                                amplitude=2.0, seed=3)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_degenerate_steps(L, O, synth, mode):
+    """Cases the method reduces to a closed form: an empty mask (b = 0, so v <- (1 - 2 eps) v and
+    E_data = 0); identical images from v = 0 (no residual: v stays 0 and E = 0); one time step
+    (T = 1) and the smallest grid (2 x 2 x 2) against the oracle."""
+    code, _ = K_MODES[mode]
+    shape = (12, 10, 16)
+    Z, Y, X = shape
+    pair = _pair_centred(synth, shape)
+    v0 = synth.smooth_velocity(3, shape, 1.5, seed=6)
+    p = L.default_params(X, Y, Z, T=3, k_mode=code)
+    eps = np.float32(p.epsilon)
+    # empty mask
+    with L.Lddmm(p, _dev(pair.I0), _dev(pair.I1), _dev(np.zeros(shape, np.float32))) as ctx:
+        ctx.set_velocity(_dev(v0))
+        e = ctx.step()
+        v1 = ctx.get_velocity()
+    ref = O.lddmm_step(v0, pair.I0, pair.I1, np.zeros(shape), O.Params(T=3))
+    assert e["data"] == 0.0
+    assert abs(e["reg"] - ref.E_reg) <= 1e-5 * ref.E_reg
+    assert _rel(v1, v0 - eps * (np.float32(2) * v0)) < 1e-6
+    # identical images from v = 0
+    with L.Lddmm(p, _dev(pair.I0), _dev(pair.I0), _dev(pair.M)) as ctx:
+        e = ctx.step()
+        v1 = ctx.get_velocity()
+    assert e["total"] == 0.0 and not v1.any()
+    # T = 1, and the smallest grid
+    rng = np.random.default_rng(9)
+    tiny = [rng.random((2, 2, 2)).astype(np.float32) for _ in range(2)] + [np.ones((2, 2, 2), np.float32)]
+    for shp, T, (I0, I1, M) in (((12, 10, 16), 1, (pair.I0, pair.I1, pair.M)),
+                                ((2, 2, 2), 2, tiny)):
+        z, y, x = shp
+        vv = synth.smooth_velocity(T, shp, 0.5, seed=7)
+        pp = L.default_params(x, y, z, T=T, k_mode=code)
+        ref = O.lddmm_step(vv, I0, I1, M, O.Params(T=T))
+        with L.Lddmm(pp, _dev(I0), _dev(I1), _dev(M)) as ctx:
+            ctx.set_velocity(_dev(vv))
+            e = ctx.step()
+            v1 = ctx.get_velocity()
+        assert _rel(v1, ref.v_new) < 1e-4
+        assert abs(e["reg"] - ref.E_reg) <= 1e-5 * max(ref.E_reg, 1e-30)
+        assert abs(e["data"] - ref.E_data) <= 1e-5 * max(ref.E_data, 1e-30) + 1e-12
+
+
 def test_twenty_iterations_config1(L, O, synth):
     pair = _pair_small(synth)
     T = 10

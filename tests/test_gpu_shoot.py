@@ -80,3 +80,19 @@ def test_shoot_rejects_bf16_storage_and_rk4(L, synth):
             with pytest.raises(L.LddmmError) as ei:
                 ctx.shoot(v0)
             assert ei.value.code == L.LDDMM_ERR_INVALID_ARG
+
+
+def test_shoot_degenerate_cases(L, synth):
+    """T = 1 keeps v_0 alone; v_0 = 0 shoots the zero field (no momentum)."""
+    shape = (16, 12, 20)
+    pair = synth.ellipsoid_pair(shape=shape, seed=0)
+    v0 = synth.smooth_velocity(1, shape, 2.0, seed=3)[0]
+    p = L.default_params(20, 12, 16, T=1)
+    with L.Lddmm(p, _dev(pair.I0), _dev(pair.I1), _dev(pair.M)) as ctx:
+        ctx.shoot(_dev(v0))
+        assert np.array_equal(ctx.get_velocity()[0], v0)
+    p = L.default_params(20, 12, 16, T=4)
+    with L.Lddmm(p, _dev(pair.I0), _dev(pair.I1), _dev(pair.M)) as ctx:
+        ctx.set_velocity(_dev(np.ones((4, 3) + shape, np.float32)))
+        ctx.shoot(_dev(np.zeros_like(v0)))
+        assert not ctx.get_velocity().any()
