@@ -57,6 +57,25 @@ def test_transport_of_momentum_under_a_translation_and_a_stretch(S):
     assert np.allclose(got[1:], s * m0[1:, :, :, 8:12], atol=1e-12)
 
 
+def test_transport_under_a_shear_at_anisotropic_spacing(S):
+    """u_x = c y (voxels) with spacing h: in physical units d phi_x / d y = c h_x / h_y, so
+    D phi = [[1, c hx/hy, 0], [0, 1, 0], [0, 0, 1]] and |D phi| = 1; for a constant m0,
+    (D phi)^T m0 = (m_x, m_y + c (hx/hy) m_x, m_z).  A transposed Jacobian or an inverted
+    spacing ratio gives a different m_x or m_y."""
+    shape = (5, 12, 9)
+    h = (0.5, 2.0, 1.0)
+    c = 0.2
+    m0 = np.broadcast_to(np.array([1.5, -0.7, 0.4])[:, None, None, None], (3,) + shape).copy()
+    y = np.arange(12)[None, :, None] * np.ones(shape)
+    u = np.zeros((3,) + shape)
+    u[0] = c * (y - 6.0)
+    got = S.transport_momentum(m0, u, h)[:, :, 1:-1, 3:6]   # away from the clamped faces
+    r = c * h[0] / h[1]
+    assert np.allclose(got[0], 1.5, atol=1e-12)
+    assert np.allclose(got[1], -0.7 + r * 1.5, atol=1e-12)
+    assert np.allclose(got[2], 0.4, atol=1e-12)
+
+
 def test_zero_and_constant_fields_are_fixed_points(S):
     from oracle import lddmm as O
     p = O.Params(T=5)
