@@ -243,9 +243,8 @@ def run_ours(args):
     for _ in range(args.warmup):
         ctx.step(want_energy=False)
     torch.cuda.synchronize()
-    # timed region
-    launches_per_step = T * 11 + 8
-    ctx.profile_start(launches_per_step * args.steps + 64)
+    # timed region: K steps with no instrumentation between the kernels (an event pair around
+    # every launch adds about 5% to the step)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -261,8 +260,19 @@ def run_ours(args):
     barrier(ws)
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    prof = ctx.profile_stop()
     ms_max = max_over_ranks(ws, ms)
+    # per-kernel launch times (the kernel table and the roofline): the same K steps again, with
+    # a CUDA-event pair around every launch on the context's stream
+    launches_per_step = T * 11 + 8
+    ctx.profile_start(launches_per_step * args.steps + 64)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ctx.step(want_energy=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_prof = ev0.elapsed_time(ev1)
+    prof = ctx.profile_stop()
     value = ws * args.steps / (ms_max / 1000.0)
     e_last = ctx.energy()
     extras = None
@@ -301,20 +311,23 @@ def run_ours(args):
         peak = peaks["hbm_gbs"]
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": name,
-                "peak_source": src + " (copy bandwidth)"}
+                "peak_source": src + " (copy bandwidth)",
+                "launch_time": LAUNCH_TIME}
     elif alg["bound"] == "tensor":
         achieved = alg["flops"] / avg_s / 1e12
         peak = peaks["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": name,
-                "peak_source": src + " (bf16 sustained)"}
+                "peak_source": src + " (bf16 sustained)",
+                "launch_time": LAUNCH_TIME}
     else:
         sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x clock
         achieved = alg["flops"] / avg_s / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": name,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz}
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz,
+                "launch_time": LAUNCH_TIME}
     # CPU baseline: the oracle, one thread, on half the grid at T=1
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
@@ -335,6 +348,7 @@ def run_ours(args):
                        "l2": "working set %.1f GB > L2 (no flush)" % (
                            (2 * T * 3 + 2 * T + 20) * N * 4 / 1e9)},
             "clocks": clk, "e2e": e2e, "gpu_launches": int(sum(v[0] for v in prof.values())),
+            "profiled_ms_per_step": ms_prof / args.steps,
             "roofline": roof, "cpu_baseline": cpu,
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 3),
                             "share": round(v[1] / sum(x[1] for x in prof.values()), 4)}
@@ -342,6 +356,10 @@ def run_ours(args):
             "energy_after": e_last["total"], "extras": extras}
     print(json.dumps(line))
     return 0
+
+
+LAUNCH_TIME = ("mean of CUDA-event pairs around each launch on the launching stream, over a "
+               "second run of the same K steps after the timed one")
 
 
 def _time_steps(L, params, I0, I1, M, stream, warm=2, steps=5):
