@@ -96,3 +96,20 @@ def test_shoot_degenerate_cases(L, synth):
         ctx.set_velocity(_dev(np.ones((4, 3) + shape, np.float32)))
         ctx.shoot(_dev(np.zeros_like(v0)))
         assert not ctx.get_velocity().any()
+
+
+def test_shoot_full_size_constant_field(L):
+    """At 264 x 160 x 228, T = 10, bf16x3 K (the benchmark's configuration): a spatially
+    constant v_0 is a fixed point of the shooting (the displacement stays constant, so
+    D phi = I and m_0 o phi = m_0 = gamma^2 v_0, and K m_0 = v_0)."""
+    shape = (228, 160, 264)
+    ones = torch.ones(shape, device="cuda")
+    p = L.default_params(264, 160, 228, T=10, k_mode=1)
+    c = torch.tensor([0.8, -1.5, 2.25], device="cuda")
+    v0 = (c[:, None, None, None] * torch.ones((3,) + shape, device="cuda")).contiguous()
+    with L.Lddmm(p, ones, ones, ones) as ctx:
+        ctx.shoot(v0)
+        v = torch.empty((10, 3) + shape, device="cuda")
+        ctx.get_velocity(v)
+    err = (v - v0[None]).abs().max().item()
+    assert err <= 1e-4 * 2.25, err
