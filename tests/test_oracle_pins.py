@@ -96,6 +96,33 @@ def test_zero_velocity_gives_identity_maps():
     np.testing.assert_allclose(r.E_data, ((I0 - I1) ** 2).sum() / p.sigma ** 2, rtol=1e-14)
 
 
+def test_first_step_residual_in_closed_form():
+    """From v = 0 the maps are the identity, so b_j = (2/sigma^2) M (I0 - I1) grad_h I0 for every
+    j and v_1 = eps K b (Beg's gradient 2v - K b at v = 0).  I0 is a quadratic, on which central
+    differences are exact: inside the grid grad_h I0 = (0.01 (2x - z) / hx, 0.04 y / hy,
+    -0.01 x / hz).  Anisotropic h and a random weight M make a wrong sign, a dropped weight or
+    spacing, or swapped components fail."""
+    shape = (6, 7, 8)
+    h = (0.5, 2.0, 1.25)
+    p = O.Params(T=3, h=h)
+    rng = _rng(11)
+    z, y, x = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in shape], indexing="ij")
+    I0 = 0.01 * (x * x + 2 * y * y - z * x) + 0.3
+    I1 = rng.uniform(0.0, 1.0, shape)
+    M = rng.uniform(0.2, 1.0, shape)
+    r = O.lddmm_step(np.zeros((3, 3) + shape), I0, I1, M, p)
+    g = [0.01 * (2 * x - z) / h[0], 0.04 * y / h[1], -0.01 * x / h[2]]
+    inner = (slice(1, -1),) * 3
+    for j in range(3):
+        for e in range(3):
+            ref = 2.0 / p.sigma ** 2 * M * (I0 - I1) * g[e]
+            np.testing.assert_allclose(r.b[j, e][inner], ref[inner], rtol=1e-12, atol=1e-12)
+        for e in range(3):
+            np.testing.assert_allclose(r.v_new[j, e], p.epsilon * O.apply_K(r.b[j, e], p.alpha,
+                                                                           p.gamma, h),
+                                       rtol=1e-12, atol=1e-15)
+
+
 def test_constant_velocity_is_an_exact_translation():
     shape = (8, 9, 10)
     T = 5
