@@ -123,6 +123,43 @@ def test_first_step_residual_in_closed_form():
                                        rtol=1e-12, atol=1e-15)
 
 
+def test_empty_mask_update_is_pure_shrinkage():
+    """With M = 0 there is no residual (b = 0), so Beg's gradient is 2 v and one step gives
+    v_1 = (1 - 2 eps) v exactly, with E_data = 0."""
+    shape = (6, 5, 7)
+    I0, I1 = _blob_pair(shape)
+    v = _rng(12).normal(size=(3, 3) + shape)
+    p = O.Params(T=3, h=(1.0, 0.5, 2.0))
+    r = O.lddmm_step(v, I0, I1, np.zeros(shape), p)
+    assert r.E_data == 0.0 and not r.b.any()
+    np.testing.assert_allclose(r.v_new, (1.0 - 2.0 * p.epsilon) * v, rtol=1e-15, atol=0)
+
+
+def test_W_carries_the_jacobian_of_an_affine_flow():
+    """For v_j(x) = A (x - c) the backward maps are affine, phi_{j,1}(x) = B^(T-j) (x - c) + c with
+    B = I + dt A (trilinear interpolation and central differences are exact on affine fields), so
+    away from the clamped faces W_j = M det(B)^(T-j) for a constant M."""
+    n, T = 20, 4
+    shape = (n, n, n)
+    A = np.array([[0.03, -0.02, 0.01], [0.015, -0.025, 0.02], [-0.01, 0.02, 0.02]])
+    c = (n - 1) / 2.0
+    z, y, x = np.meshgrid(*[np.arange(n, dtype=np.float64)] * 3, indexing="ij")
+    q = np.stack([x - c, y - c, z - c])
+    vel = np.einsum("de,e...->d...", A, q)
+    v = np.broadcast_to(vel, (T, 3) + shape).copy()
+    p = O.Params(T=T)
+    M = np.full(shape, 0.75)
+    J1, W, u01, _ = O.backward_sweep(v, np.zeros(shape), M, p)
+    detB = np.linalg.det(np.eye(3) + A / T)
+    inner = (slice(6, -6),) * 3
+    for j in range(T):
+        np.testing.assert_allclose(W[j][inner], 0.75 * detB ** (T - j), rtol=1e-12)
+    Bt = np.linalg.matrix_power(np.eye(3) + A / T, T)
+    ref = np.einsum("de,e...->d...", Bt - np.eye(3), q)
+    np.testing.assert_allclose(u01[(slice(None),) + inner], ref[(slice(None),) + inner],
+                               atol=1e-12)
+
+
 def test_constant_velocity_is_an_exact_translation():
     shape = (8, 9, 10)
     T = 5
