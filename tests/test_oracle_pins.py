@@ -384,9 +384,39 @@ def test_warp_identity_and_shift():
     np.testing.assert_array_equal(O.warp(f, u), f)
     u[2] = 1.0
     np.testing.assert_allclose(O.warp(f, u), f[np.clip(np.arange(5) + 1, 0, 4)], atol=1e-14)
+    u[2] = 0.0
+    u[0] = 1.0                                   # (id + u)(x) = x + 1 along x
+    u[1] = -1.0                                  # and y - 1
+    ref = f[:, np.clip(np.arange(6) - 1, 0, 5)][:, :, np.clip(np.arange(7) + 1, 0, 6)]
+    np.testing.assert_allclose(O.warp(f, u), ref, atol=1e-14)
 
 
 # ---------------------------------------------------------------- multiscale
+
+def test_register_levels_measure_the_same_energy():
+    """The energy is a discretised integral, so a coarse level (block means, spacing f h) must
+    give the same value as the fine grid where the discretisation is exact: for images that are
+    constant on 2x2x2 blocks and v = 0 the data terms agree, and for a spatially constant v the
+    regulariser terms agree (|L v|^2 = gamma^2 |v|^2 per unit volume)."""
+    rng = _rng(15)
+    coarse = (4, 3, 5)
+    shape = (8, 6, 10)
+    h = (1.0, 1.5, 0.5)
+    up = lambda a: np.repeat(np.repeat(np.repeat(a, 2, 0), 2, 1), 2, 2)
+    I0 = up(rng.random(coarse))
+    I1 = up(rng.random(coarse))
+    M = np.ones(shape)
+    p = O.Params(T=2, h=h)
+    _, e2, _ = O.register(I0, I1, M, p, 1, factors=(2,))
+    _, e1, _ = O.register(I0, I1, M, p, 1, factors=(1,))
+    assert e2[0][1] == 0.0 and e1[0][1] == 0.0
+    np.testing.assert_allclose(e2[0][2], e1[0][2], rtol=1e-12)
+    c = np.array([0.4, -0.3, 0.2])[None, :, None, None, None]
+    _, e2, _ = O.register(I0, I1, M, p, 1, factors=(2,), v0=c * np.ones((2, 3) + coarse))
+    _, e1, _ = O.register(I0, I1, M, p, 1, factors=(1,), v0=c * np.ones((2, 3) + shape))
+    np.testing.assert_allclose(e2[0][1], e1[0][1], rtol=1e-12)
+    np.testing.assert_allclose(e1[0][1], (c ** 2).sum() * np.prod(shape) * np.prod(h), rtol=1e-12)
+
 
 def test_downsample_block_mean():
     f = np.arange(4 * 4 * 6, dtype=float).reshape(4, 4, 6)

@@ -78,3 +78,12 @@ def test_opening_removes_grains_and_keeps_a_large_ball(P):
     got = P.mask_morphology(m.astype(float), 0.5, 1, 0)
     assert not got[1, 1, 1] and not got[2, 20, 5]
     assert np.array_equal(got, P.dilate_brute(P.erode_brute(big, 1), 1))
+
+
+def test_threshold_is_strict(P):
+    """The rough mask is [I > threshold]: voxels exactly at the threshold are background."""
+    I = np.zeros((5, 5, 5))
+    I[1:4, 1:4, 1:4] = 0.5
+    I[2, 2, 2] = 0.7
+    m = P.mask_morphology(I, 0.5, 0, 0)
+    assert m.sum() == 1 and m[2, 2, 2]
