@@ -81,6 +81,17 @@ def test_adam_first_step_is_signed_lr():
     np.testing.assert_allclose(w, -0.01 * np.sign(g), rtol=1e-6)
 
 
+def test_adam_epsilon_is_added_to_the_root():
+    """Adam's denominator is sqrt(v_hat) + eps (Kingma and Ba): a first step with |g| = eps moves
+    by lr / 2, and a second step with the same gradient again by lr |g| / (|g| + eps)."""
+    eps = 1e-6
+    g = np.array([eps, -eps])
+    w, m, v = S.adam(np.zeros(2), g, np.zeros(2), np.zeros(2), 0.01, 0.9, 0.999, eps, 1)
+    np.testing.assert_allclose(w, -0.005 * np.sign(g), rtol=1e-9)
+    w, m, v = S.adam(w, g, m, v, 0.01, 0.9, 0.999, eps, 2)
+    np.testing.assert_allclose(w, -0.01 * np.sign(g), rtol=1e-9)
+
+
 def test_layer_shapes_of_the_four_level_network():
     sh = S.layer_shapes((16, 32, 64, 128), 2, 3)
     assert sh[0] == (16, 2, 3) and sh[7] == (128, 128, 3)
