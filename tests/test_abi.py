@@ -75,3 +75,24 @@ def test_default_params(lib):
     assert (p.nx, p.ny, p.nz, p.T) == (264, 160, 228, 10)
     assert abs(p.alpha - 0.02) < 1e-9 and p.gamma == 1.0 and abs(p.sigma - 0.1) < 1e-7
     assert ctypes.sizeof(L.lddmm_energy) == 48
+
+
+def test_context_free_entry_points_reject_bad_arguments_without_gpu(lib):
+    """The §2.2 preprocessing and the context entry points validate their arguments on the host
+    (sizes, radii, bin and point counts, NULL pointers) before any CUDA call."""
+    from paper_1605_02060_gb300 import lddmm as L
+    a = np.zeros(64, np.float32)
+    p = a.ctypes.data_as(ctypes.c_void_p)
+    cases = [
+        lambda: lib.lddmm_histogram_match(p, p, p, p, 64, 0, 8, p, None),      # bins < 1
+        lambda: lib.lddmm_histogram_match(p, p, p, p, 64, 32, 65, p, None),    # points > 64
+        lambda: lib.lddmm_histogram_match(p, p, p, p, 0, 32, 8, p, None),      # n = 0
+        lambda: lib.lddmm_histogram_match(None, p, p, p, 64, 32, 8, p, None),  # NULL image
+        lambda: lib.lddmm_mask_morphology(p, 4, 4, 4, 0.5, 17, 1, p, None),    # r_open > 16
+        lambda: lib.lddmm_mask_morphology(p, 0, 4, 4, 0.5, 1, 1, p, None),     # empty grid
+        lambda: lib.lddmm_shoot(None, p),
+        lambda: lib.lddmm_surface_distance(None, p, p, (ctypes.c_double * 4)()),
+        lambda: lib.lddmm_landmark_error(None, p, p, 1, p),
+    ]
+    for i, call in enumerate(cases):
+        assert call() == L.LDDMM_ERR_INVALID_ARG, i
