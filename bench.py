@@ -53,8 +53,9 @@ def _csrc_hash():
     return h.hexdigest()[:16]
 
 
-# Algorithmic bytes (or flops) per voxel for one launch of each kernel (fp32 storage);
-# the derivation is in the design notes: each field is read or written once per launch.
+# Algorithmic bytes (or flops) per voxel for one launch of each kernel (fp32 storage): each
+# field the kernel reads or writes counts once per launch, a trilinear gather counts the
+# gathered field once (the displacements are small, so the corners hit L1/L2).
 def algorithmic(kernel, N, dims, kmode, T=10, peaks=None):
     X, Y, Z = dims
     B = {"flow_back_disp": 36, "flow_back_terms": 28, "fwd_residual": 36,
