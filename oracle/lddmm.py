@@ -18,7 +18,7 @@ via masked LDDMM", SPIE 2016):
       v_t <- v_t - eps grad_t,
   with J0_t = I0 o phi_t0, J1_t = I1 o phi_t1.
 
-Readings where the paper is silent (each is also listed in the design notes):
+Readings where the paper is silent:
 * Time discretisation: T steps, dt = 1/T, first-order semi-Lagrangian flows (the paper uses
   4 steps of RK4, §2.4; this build uses T steps of one trilinear lookup each):
       phi_{j,1}(x) = phi_{j+1,1}(x + dt v_j(x)),  phi_{T,1} = id   (backward sweep)
