@@ -20,7 +20,8 @@ via masked LDDMM", SPIE 2016):
 
 Readings where the paper is silent:
 * Time discretisation: T steps, dt = 1/T, first-order semi-Lagrangian flows (the paper uses
-  4 steps of RK4, §2.4; this build uses T steps of one trilinear lookup each):
+  4 steps of RK4, §2.4; the default here is T steps of one trilinear lookup each, with RK4
+  available as integrator="rk4"):
       phi_{j,1}(x) = phi_{j+1,1}(x + dt v_j(x)),  phi_{T,1} = id   (backward sweep)
       phi_{j+1,0}(x) = phi_{j,0}(x - dt v_j(x)),  phi_{0,0} = id   (forward sweep)
   Maps are stored as displacements u = phi - id in voxel units of the grid; velocities are in

@@ -10,7 +10,7 @@ EPDiff  d m / dt = - ad*_v m  has the solution
     m_t = Ad*_{phi_t^-1} m_0 = |D phi_{t,0}| (D phi_{t,0})^T (m_0 o phi_{t,0}),
 the initial momentum transported by the flow (phi_{t,0} carries time-t positions back to 0).
 
-Readings (the paper does not shoot; these are the discrete choices of this build):
+Readings (the paper does not shoot; these are the discrete choices made here):
 * phi_{j,0} comes from the same semi-Lagrangian steps as the registration's forward sweep:
   phi_{j+1,0}(x) = phi_{j,0}(x - dt v_j(x)), trilinear, clamp to edge; dt = 1/T.
 * m_0 o phi is a trilinear lookup (clamp to edge); D phi is taken by central differences inside
