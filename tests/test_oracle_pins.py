@@ -511,3 +511,86 @@ def test_rk4_equals_one_lookup_for_a_spatially_constant_field():
     a = O.backward_sweep(v, I1, I1, O.Params(T=T, integrator="rk4"))
     b = O.backward_sweep(v, I1, I1, O.Params(T=T))
     assert np.allclose(a[2], b[2], atol=1e-12) and np.allclose(a[0], b[0], atol=1e-12)
+
+
+def _affine_chain(A, dt, sign, T, backward):
+    """Products of I + sign dt A_j: backward P_j = P_{j+1} (I + dt A_j) with P_T = I; forward
+    Q_{j+1} = Q_j (I - dt A_j) with Q_0 = I."""
+    out = [None] * (T + 1)
+    if backward:
+        out[T] = np.eye(3)
+        for j in range(T - 1, -1, -1):
+            out[j] = out[j + 1] @ (np.eye(3) + sign * dt * A[j])
+    else:
+        out[0] = np.eye(3)
+        for j in range(T):
+            out[j + 1] = out[j] @ (np.eye(3) + sign * dt * A[j])
+    return out
+
+
+def test_body_force_at_every_step_of_a_time_varying_affine_flow():
+    """For a velocity that is affine in space with a different matrix at every step,
+    v_j(x) = H A_j (x - c) (H = diag(h); A_j in voxels per unit time), every map is affine and
+    every trilinear lookup and central difference is exact away from the clamped faces:
+        phi_{j,1}(x) = c + P_j (x - c),  P_j = P_{j+1} (I + dt A_j),  P_T = I,
+        phi_{j,0}(x) = c + Q_j (x - c),  Q_{j+1} = Q_j (I - dt A_j),  Q_0 = I.
+    With linear I0 = a0 + g0.x, I1 and M the body force of Beg's gradient at step j is
+        b_j = (2/sigma^2) M(phi_{j,1}) det(P_j) (I0(phi_{j,0}) - I1(phi_{j,1})) (Q_j^T g0) / h,
+    the spatial gradient of the deformed template I0 o phi_{j,0} (not the template's gradient
+    carried along, g0), paired with the target-side terms of the same time t_j.  Pairing J0_j with
+    W_{j+1} and J1_{j+1}, taking (grad I0) o phi, or any dropped chain factor fails this at some j.
+    The update is then v - eps (2 v - K b) with K the (separately pinned) spectral operator."""
+    T = 4
+    dt = 1.0 / T
+    shape = (30, 32, 36)                                   # Z, Y, X
+    h = np.array([1.0, 0.8, 1.25])
+    rng = _rng(21)
+    A = [0.04 * rng.standard_normal((3, 3)) for _ in range(T)]
+    A[1] += 0.06 * np.eye(3)                                # det(I + dt A_j) far from 1
+    A[2] -= 0.05 * np.eye(3)
+    c = np.array([(n - 1) / 2.0 for n in shape[::-1]])     # (x, y, z) centre
+    z, y, x = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in shape], indexing="ij")
+    q = np.stack([x - c[0], y - c[1], z - c[2]])
+    v = np.stack([np.einsum("de,e...->d...", A[j], q) * h[:, None, None, None]
+                  for j in range(T)])
+    dmax = max(float(np.abs(dt * np.einsum("de,e...->d...", A[j], q)).max()) for j in range(T))
+    assert dmax < 1.0
+    m = T * (int(np.ceil(dmax)) + 1) + 2                   # exactness margin from the faces
+    inner = (slice(m, -m),) * 3
+    assert all(n - 2 * m >= 4 for n in shape)
+    g0, g1, gm = np.array([0.02, -0.015, 0.03]), np.array([-0.01, 0.025, 0.012]), \
+        np.array([0.01, 0.006, -0.008])
+    I0 = 0.4 + g0[0] * x + g0[1] * y + g0[2] * z
+    I1 = 0.1 + g1[0] * x + g1[1] * y + g1[2] * z
+    M = 0.9 + gm[0] * x + gm[1] * y + gm[2] * z
+    p = O.Params(T=T, h=tuple(h), epsilon=0.01)
+    r = O.lddmm_step(v, I0, I1, M, p)
+
+    P = _affine_chain(A, dt, +1.0, T, backward=True)
+    Q = _affine_chain(A, dt, -1.0, T, backward=False)
+
+    def lin(a, g, Mat):                                   # a + g . (c + Mat q)
+        pos = c[:, None, None, None] + np.einsum("de,e...->d...", Mat, q)
+        return a + np.einsum("d,d...->...", g, pos)
+
+    for j in range(T):
+        J1 = lin(0.1, g1, P[j])
+        W = lin(0.9, gm, P[j]) * np.linalg.det(P[j])
+        J0 = lin(0.4, g0, Q[j])
+        grad = Q[j].T @ g0
+        np.testing.assert_allclose(r.J1[j][inner], J1[inner], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(r.W[j][inner], W[inner], rtol=1e-12, atol=0)
+        for e in range(3):
+            ref = 2.0 / p.sigma ** 2 * W * (J0 - J1) * grad[e] / h[e]
+            np.testing.assert_allclose(r.b[j, e][inner], ref[inner], rtol=0,
+                                       atol=1e-10 * float(np.abs(ref[inner]).max()))
+    u01 = np.einsum("de,e...->d...", P[0] - np.eye(3), q)
+    u10 = np.einsum("de,e...->d...", Q[T] - np.eye(3), q)
+    np.testing.assert_allclose(r.u01[(slice(None),) + inner], u01[(slice(None),) + inner], atol=1e-11)
+    np.testing.assert_allclose(r.u10[(slice(None),) + inner], u10[(slice(None),) + inner], atol=1e-11)
+    np.testing.assert_allclose(r.J0T[inner], lin(0.4, g0, Q[T])[inner], atol=1e-12)
+    for j in range(T):
+        for e in range(3):
+            Kb = O.apply_K(r.b[j, e], p.alpha, p.gamma, p.h)
+            np.testing.assert_allclose(r.v_new[j, e], v[j, e] - p.epsilon * (2 * v[j, e] - Kb),
+                                       rtol=1e-13, atol=1e-13)
