@@ -254,9 +254,16 @@ int lddmm_net_conv3d_fwd(const float* x, const void* w_bf16, const float* bias, 
  * bf16 (the transposed, flipped kernel). */
 int lddmm_net_conv3d_dgrad(const float* dy, const void* w_bf16, void* wT_scratch, float* dx, int B,
                            int Ci, int Co, int n, int ksize, void* stream);
-/* dw += weight gradient (float32 [Co][Ci][k^3]), db += bias gradient (NULL: skipped). */
-int lddmm_net_conv3d_wgrad(const float* x, const float* dy, float* dw, float* db, int B, int Ci,
-                           int Co, int n, int ksize, void* stream);
+/* Floats of scratch that lddmm_net_conv3d_wgrad needs for this shape (LDDMM_ERR_INVALID_ARG on
+ * a bad shape). */
+int64_t lddmm_net_conv3d_wgrad_scratch(int B, int Ci, int Co, int n, int ksize);
+/* dw += weight gradient (float32 [Co][Ci][k^3]), db += bias gradient (NULL: skipped).  The sums
+ * run in a fixed order through partial sums in `scratch` (device, scratch_floats >= the size
+ * lddmm_net_conv3d_wgrad_scratch gives, else LDDMM_ERR_INVALID_ARG), so repeated calls on the same
+ * inputs give the same bits. */
+int lddmm_net_conv3d_wgrad(const float* x, const float* dy, float* dw, float* db, float* scratch,
+                           int64_t scratch_floats, int B, int Ci, int Co, int n, int ksize,
+                           void* stream);
 /* dy[i] = 0 where y[i] <= 0 (ReLU backward on the stored output). */
 int lddmm_net_relu_bwd(float* dy, const float* y, int64_t count, void* stream);
 /* 2x average pooling of BC volumes of n^3 (backward: src = coarse gradient, dst = fine). */

@@ -9,6 +9,7 @@
 //   conv_dgrad dx[b,ci,v] = sum_co sum_t w[co,ci,t] dy[b,co,v-o(t)]  (= conv_fwd with the
 //              transposed, flipped kernel, since o(26-t) = -o(t))
 //   conv_wgrad dw[co,ci,t] += sum_b sum_v dy[b,co,v] x[b,ci,v+o(t)],  db[co] += sum dy[b,co,v]
+//              (fixed-order partial sums in caller scratch: the same bits on every run)
 // plus 2x average pooling, 2x nearest upsampling, channel concatenation, ReLU backward, the MSE
 // loss and Adam.  Forward tiles: 8x8x4 output voxels x 16 output channels per block, input
 // channels staged 8 at a time with a one-voxel halo in shared memory.
@@ -114,58 +115,82 @@ __global__ void k_transpose_flip(const __nv_bfloat16* __restrict__ w, __nv_bfloa
   wT[i] = w[((size_t)co * Ci + ci) * taps + (taps - 1 - t)];
 }
 
-// Weight gradient: one block per (tile, input channel, batch); thread = (output channel, tap)
-// pairs looping over the tile's voxels; partial sums added to dw with atomics.
+// Weight gradient, deterministic: block (g, ci * co-tile) sums, in a fixed order, the
+// (batch, tile) units g, g + G, g + 2G, ... into one partial per (output channel, tap), written
+// to part[g][co][ci][t]; k_wgrad_reduce then adds the G partials of every weight in order g = 0..G-1.
+// No floating-point atomics, so the result is the same on every run.
 __global__ void __launch_bounds__(512) k_conv_wgrad(const float* __restrict__ x,
                                                     const float* __restrict__ dy,
-                                                    float* __restrict__ dw, int Ci, int Co, int n,
-                                                    int ks) {
+                                                    float* __restrict__ part, int B, int Ci, int Co,
+                                                    int n, int ks, int G) {
   __shared__ float xs[HV];
   __shared__ float dys[CT][NTV];
   const int tid = threadIdx.x;
-  const int ntx = (n + BX - 1) / BX, nty = (n + BY - 1) / BY;
-  const int tile = blockIdx.x;
-  const int tx0 = (tile % ntx) * BX, ty0 = ((tile / ntx) % nty) * BY, tz0 = (tile / (ntx * nty)) * BZ;
+  const int ntx = (n + BX - 1) / BX, nty = (n + BY - 1) / BY, ntz = (n + BZ - 1) / BZ;
+  const int tiles = ntx * nty * ntz;
+  const int g = blockIdx.x;
   const int ci = blockIdx.y % Ci, cot = blockIdx.y / Ci;
-  const int co0 = cot * CT, b = blockIdx.z;
+  const int co0 = cot * CT;
   const size_t nv = (size_t)n * n * n;
   const int taps = ks * ks * ks;
-  for (int i = tid; i < HV; i += blockDim.x) {
-    const int hx = i % HXn, hy = (i / HXn) % HYn, hz = i / (HXn * HYn);
-    xs[i] = xval(x + ((size_t)b * Ci + ci) * nv, n, tx0 + hx - 1, ty0 + hy - 1, tz0 + hz - 1);
-  }
-  for (int i = tid; i < CT * NTV; i += blockDim.x) {
-    const int c = i / NTV, vv = i % NTV;
-    const int lx = vv % BX, ly = (vv / BX) % BY, lz = vv / (BX * BY);
-    const int gx = tx0 + lx, gy = ty0 + ly, gz = tz0 + lz;
-    const int co = co0 + c;
-    dys[c][vv] = (co < Co && gx < n && gy < n && gz < n)
-                     ? dy[((size_t)b * Co + co) * nv + ((size_t)gz * n + gy) * n + gx]
-                     : 0.f;
-  }
-  __syncthreads();
-  if (tid < CT * taps) {
-    const int c = tid / taps, t = tid % taps;
-    int ox, oy, oz;
-    if (ks == 3) { ox = t % 3 - 1; oy = (t / 3) % 3 - 1; oz = t / 9 - 1; }
-    else { ox = oy = oz = 0; }
-    float s = 0.f;
-    for (int vv = 0; vv < NTV; ++vv) {
-      const int lx = vv % BX, ly = (vv / BX) % BY, lz = vv / (BX * BY);
-      s = fmaf(dys[c][vv], xs[((lz + 1 + oz) * HYn + (ly + 1 + oy)) * HXn + (lx + 1 + ox)], s);
+  const int c = tid / taps, t = tid % taps;
+  int ox = 0, oy = 0, oz = 0;
+  if (ks == 3) { ox = t % 3 - 1; oy = (t / 3) % 3 - 1; oz = t / 9 - 1; }
+  float s = 0.f;
+  for (int u = g; u < tiles * B; u += G) {
+    const int b = u / tiles, tile = u % tiles;
+    const int tx0 = (tile % ntx) * BX, ty0 = ((tile / ntx) % nty) * BY, tz0 = (tile / (ntx * nty)) * BZ;
+    for (int i = tid; i < HV; i += blockDim.x) {
+      const int hx = i % HXn, hy = (i / HXn) % HYn, hz = i / (HXn * HYn);
+      xs[i] = xval(x + ((size_t)b * Ci + ci) * nv, n, tx0 + hx - 1, ty0 + hy - 1, tz0 + hz - 1);
     }
-    const int co = co0 + c;
-    if (co < Co && s != 0.f) atomicAdd(dw + ((size_t)co * Ci + ci) * taps + t, s);
+    for (int i = tid; i < CT * NTV; i += blockDim.x) {
+      const int cc = i / NTV, vv = i % NTV;
+      const int lx = vv % BX, ly = (vv / BX) % BY, lz = vv / (BX * BY);
+      const int gx = tx0 + lx, gy = ty0 + ly, gz = tz0 + lz;
+      const int co = co0 + cc;
+      dys[cc][vv] = (co < Co && gx < n && gy < n && gz < n)
+                        ? dy[((size_t)b * Co + co) * nv + ((size_t)gz * n + gy) * n + gx]
+                        : 0.f;
+    }
+    __syncthreads();
+    if (tid < CT * taps) {
+      for (int vv = 0; vv < NTV; ++vv) {
+        const int lx = vv % BX, ly = (vv / BX) % BY, lz = vv / (BX * BY);
+        s = fmaf(dys[c][vv], xs[((lz + 1 + oz) * HYn + (ly + 1 + oy)) * HXn + (lx + 1 + ox)], s);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid < CT * taps && co0 + c < Co)
+    part[(size_t)g * Co * Ci * taps + ((size_t)(co0 + c) * Ci + ci) * taps + t] = s;
+}
+
+// dw[i] += sum_{g = 0..G-1} part[g][i], in that order.
+__global__ void k_wgrad_reduce(const float* __restrict__ part, float* __restrict__ dw, int64_t count,
+                               int G) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (; i < count; i += st) {
+    float s = 0.f;
+    for (int g = 0; g < G; ++g) s += part[(size_t)g * count + i];
+    dw[i] += s;
   }
 }
 
-// db[co] += sum_{b,v} dy[b,co,v]: one block per (co, b)
-__global__ void k_bias_grad(const float* __restrict__ dy, float* __restrict__ db, int Co, int n) {
-  const int co = blockIdx.x, b = blockIdx.y;
+// Bias gradient, deterministic: block (co, g) sums the fixed chunk g of the B * n^3 values of
+// channel co (tree reduction of fixed shape) into partb[co][g]; k_bias_reduce adds them in order.
+__global__ void k_bias_partial(const float* __restrict__ dy, float* __restrict__ partb, int B, int Co,
+                               int n, int GB) {
+  const int co = blockIdx.x, g = blockIdx.y;
   const size_t nv = (size_t)n * n * n;
-  const float* p = dy + ((size_t)b * Co + co) * nv;
+  const size_t total = (size_t)B * nv, chunk = (total + GB - 1) / GB;
+  const size_t lo = (size_t)g * chunk, hi = lo + chunk < total ? lo + chunk : total;
   float s = 0.f;
-  for (size_t i = threadIdx.x; i < nv; i += blockDim.x) s += p[i];
+  for (size_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const size_t b = i / nv, v = i % nv;
+    s += dy[(b * Co + co) * nv + v];
+  }
   __shared__ float red[32];
   s = warp_sum_f(s);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -173,8 +198,16 @@ __global__ void k_bias_grad(const float* __restrict__ dy, float* __restrict__ db
   if (threadIdx.x < 32) {
     float t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
     t = warp_sum_f(t);
-    if (threadIdx.x == 0) atomicAdd(db + co, t);
+    if (threadIdx.x == 0) partb[(size_t)co * GB + g] = t;
   }
+}
+
+__global__ void k_bias_reduce(const float* __restrict__ partb, float* __restrict__ db, int Co, int GB) {
+  const int co = blockIdx.x * blockDim.x + threadIdx.x;
+  if (co >= Co) return;
+  float s = 0.f;
+  for (int g = 0; g < GB; ++g) s += partb[(size_t)co * GB + g];
+  db[co] += s;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -333,11 +366,37 @@ cudaError_t net_conv_dgrad(const float* dy, const void* w, void* wT_scratch, flo
   return net_conv_fwd(dy, wT_scratch, nullptr, dx, B, Co, Ci, n, ks, 0, 0, s);
 }
 
-cudaError_t net_conv_wgrad(const float* x, const float* dy, float* dw, float* db, int B, int Ci,
-                           int Co, int n, int ks, cudaStream_t s) {
-  dim3 grid(tiles_of(n), Ci * ((Co + CT - 1) / CT), B);
-  k_conv_wgrad<<<grid, 512, 0, s>>>(x, dy, dw, Ci, Co, n, ks);
-  if (db) k_bias_grad<<<dim3(Co, B), 256, 0, s>>>(dy, db, Co, n);
+// Partition of the weight-gradient sums: G voxel groups (about 2048 blocks in all, at most one
+// group per (batch, tile) unit), GB chunks per bias channel.
+static void wgrad_groups(int B, int Ci, int Co, int n, int* G, int* GB) {
+  const int units = tiles_of(n) * B;
+  const int cb = Ci * ((Co + CT - 1) / CT);
+  int g = (2048 + cb - 1) / cb;
+  *G = g < 1 ? 1 : (g > units ? units : g);
+  const int64_t total = (int64_t)B * n * n * n;
+  int64_t gb = (total + 8191) / 8192;
+  *GB = (int)(gb < 1 ? 1 : (gb > 64 ? 64 : gb));
+}
+
+int64_t net_conv_wgrad_scratch(int B, int Ci, int Co, int n, int ks) {
+  int G, GB;
+  wgrad_groups(B, Ci, Co, n, &G, &GB);
+  return (int64_t)G * Co * Ci * ks * ks * ks + (int64_t)Co * GB;
+}
+
+cudaError_t net_conv_wgrad(const float* x, const float* dy, float* dw, float* db, float* scratch,
+                           int B, int Ci, int Co, int n, int ks, cudaStream_t s) {
+  int G, GB;
+  wgrad_groups(B, Ci, Co, n, &G, &GB);
+  const int64_t count = (int64_t)Co * Ci * ks * ks * ks;
+  dim3 grid(G, Ci * ((Co + CT - 1) / CT));
+  k_conv_wgrad<<<grid, 512, 0, s>>>(x, dy, scratch, B, Ci, Co, n, ks, G);
+  k_wgrad_reduce<<<gs(count), 256, 0, s>>>(scratch, dw, count, G);
+  if (db) {
+    float* partb = scratch + (size_t)G * count;
+    k_bias_partial<<<dim3(Co, GB), 256, 0, s>>>(dy, partb, B, Co, n, GB);
+    k_bias_reduce<<<(Co + 127) / 128, 128, 0, s>>>(partb, db, Co, GB);
+  }
   return cudaGetLastError();
 }
 

@@ -8,8 +8,9 @@ cudaError_t net_conv_fwd(const float* x, const void* w, const float* bias, float
                          int Co, int n, int ks, int relu, int accumulate, cudaStream_t s);
 cudaError_t net_conv_dgrad(const float* dy, const void* w, void* wT_scratch, float* dx, int B,
                            int Ci, int Co, int n, int ks, cudaStream_t s);
-cudaError_t net_conv_wgrad(const float* x, const float* dy, float* dw, float* db, int B, int Ci,
-                           int Co, int n, int ks, cudaStream_t s);
+cudaError_t net_conv_wgrad(const float* x, const float* dy, float* dw, float* db, float* scratch,
+                           int B, int Ci, int Co, int n, int ks, cudaStream_t s);
+int64_t net_conv_wgrad_scratch(int B, int Ci, int Co, int n, int ks);
 cudaError_t net_relu_bwd(float* dy, const float* y, int64_t count, cudaStream_t s);
 cudaError_t net_pool_fwd(const float* x, float* y, int64_t BC, int n, cudaStream_t s);
 cudaError_t net_pool_bwd(const float* dy, float* dx, int64_t BC, int n, cudaStream_t s);
@@ -50,10 +51,17 @@ int lddmm_net_conv3d_dgrad(const float* dy, const void* w_bf16, void* wT_scratch
   return ret(net_conv_dgrad(dy, w_bf16, wT_scratch, dx, B, Ci, Co, n, ksize, (cudaStream_t)stream));
 }
 
-int lddmm_net_conv3d_wgrad(const float* x, const float* dy, float* dw, float* db, int B, int Ci,
-                           int Co, int n, int ksize, void* stream) {
-  if (!x || !dy || !dw || !shape_ok(B, Ci, Co, n, ksize)) return LDDMM_ERR_INVALID_ARG;
-  return ret(net_conv_wgrad(x, dy, dw, db, B, Ci, Co, n, ksize, (cudaStream_t)stream));
+int64_t lddmm_net_conv3d_wgrad_scratch(int B, int Ci, int Co, int n, int ksize) {
+  if (!shape_ok(B, Ci, Co, n, ksize)) return LDDMM_ERR_INVALID_ARG;
+  return net_conv_wgrad_scratch(B, Ci, Co, n, ksize);
+}
+
+int lddmm_net_conv3d_wgrad(const float* x, const float* dy, float* dw, float* db, float* scratch,
+                           int64_t scratch_floats, int B, int Ci, int Co, int n, int ksize,
+                           void* stream) {
+  if (!x || !dy || !dw || !scratch || !shape_ok(B, Ci, Co, n, ksize)) return LDDMM_ERR_INVALID_ARG;
+  if (scratch_floats < net_conv_wgrad_scratch(B, Ci, Co, n, ksize)) return LDDMM_ERR_INVALID_ARG;
+  return ret(net_conv_wgrad(x, dy, dw, db, scratch, B, Ci, Co, n, ksize, (cudaStream_t)stream));
 }
 
 int lddmm_net_relu_bwd(float* dy, const float* y, int64_t count, void* stream) {

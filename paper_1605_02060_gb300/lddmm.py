@@ -106,7 +106,9 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_int)]),
     "lddmm_net_conv3d_fwd": (ctypes.c_int, [_P, _P, _P, _P] + [ctypes.c_int] * 7 + [_P]),
     "lddmm_net_conv3d_dgrad": (ctypes.c_int, [_P, _P, _P, _P] + [ctypes.c_int] * 5 + [_P]),
-    "lddmm_net_conv3d_wgrad": (ctypes.c_int, [_P, _P, _P, _P] + [ctypes.c_int] * 5 + [_P]),
+    "lddmm_net_conv3d_wgrad_scratch": (ctypes.c_int64, [ctypes.c_int] * 5),
+    "lddmm_net_conv3d_wgrad": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int64]
+                               + [ctypes.c_int] * 5 + [_P]),
     "lddmm_net_relu_bwd": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "lddmm_net_pool2": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _P]),
     "lddmm_net_up2": (ctypes.c_int, [_P, _P] + [ctypes.c_int] * 6 + [_P]),

@@ -81,8 +81,23 @@ class UNet3D:
                 lst.append(torch.zeros_like(like))
         maxw = max(co * ci * k ** 3 for co, ci, k in self.shapes)
         self.wT = torch.empty(maxw, dtype=torch.bfloat16, device=self.dev)
+        sizes = [n >> l for l in range(len(self.chans))]
+        need = [self.lib.lddmm_net_conv3d_wgrad_scratch(batch, ci, co, sizes[self._level(i)], k)
+                for i, (co, ci, k) in enumerate(self.shapes)]
+        if min(need) < 0:
+            raise L.LddmmError(int(min(need)), "bad network shape")
+        self.wg_scratch = torch.empty(max(need), device=self.dev)
         self.step_count = 0
         self._alloc()
+
+    def _level(self, i):
+        """Pyramid level of convolution i (execution order: encoder, decoder, head)."""
+        Lv = len(self.chans)
+        if i < 2 * Lv:
+            return i // 2
+        if i < len(self.shapes) - 1:
+            return Lv - 2 - (i - 2 * Lv) // 2
+        return 0
 
     # ------------------------------------------------------------------ buffers
     def _alloc(self):
@@ -121,6 +136,7 @@ class UNet3D:
         if relu_out is not None:
             _ck(self.lib.lddmm_net_relu_bwd(_p(g_out), _p(relu_out), g_out.numel(), self.s))
         _ck(self.lib.lddmm_net_conv3d_wgrad(_p(x_in), _p(g_out), _p(self.dw[li]), _p(self.db[li]),
+                                            _p(self.wg_scratch), self.wg_scratch.numel(),
                                             self.B, ci, co, m, k, self.s))
         if g_in is not None:
             _ck(self.lib.lddmm_net_conv3d_dgrad(_p(g_out), _p(self.wb[li]), _p(self.wT), _p(g_in),
@@ -367,9 +383,11 @@ def run_warm(net, pair, target_energy, max_iters, T=10, k_mode=1, flags=0, shoot
         v = smooth_prediction(ctx, warm_start_field(net, pair, T), p.gamma)
         c, e, nev = choose_start_shot(ctx, v[0]) if shoot else choose_start(ctx, v)
         run_warm.last_start_energy = e
+        run_warm.last_energies = [e]
         it = 0
         while it < max_iters and e > target_energy:
             e = ctx.step()["total"]
+            run_warm.last_energies.append(e)
             it += 1
             if e <= target_energy:
                 break

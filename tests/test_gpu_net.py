@@ -27,6 +27,7 @@ def lib():
 
 
 P = lambda t: ctypes.c_void_p(t.data_ptr())
+L_INVALID = -1
 
 
 def _bf(a):
@@ -53,8 +54,19 @@ def test_conv_kernels_match_oracle(lib, B, Ci, Co, n, k):
     assert lib.lddmm_net_conv3d_dgrad(P(dyd), P(wbd), P(scratch), P(dx), B, Ci, Co, n, k, None) == 0
     dw = torch.zeros((Co, Ci, k ** 3), device="cuda")
     db = torch.zeros(Co, device="cuda")
-    assert lib.lddmm_net_conv3d_wgrad(P(xd), P(dyd), P(dw), P(db), B, Ci, Co, n, k, None) == 0
+    nsc = lib.lddmm_net_conv3d_wgrad_scratch(B, Ci, Co, n, k)
+    assert nsc > 0
+    wsc = torch.empty(nsc, device="cuda")
+    assert lib.lddmm_net_conv3d_wgrad(P(xd), P(dyd), P(dw), P(db), P(wsc), nsc - 1, B, Ci, Co, n, k,
+                                      None) == L_INVALID
+    assert lib.lddmm_net_conv3d_wgrad(P(xd), P(dyd), P(dw), P(db), P(wsc), nsc, B, Ci, Co, n, k,
+                                      None) == 0
+    # a second call on zeroed sums gives the same bits (fixed-order partial sums, no atomics)
+    dw2, db2 = torch.zeros_like(dw), torch.zeros_like(db)
+    assert lib.lddmm_net_conv3d_wgrad(P(xd), P(dyd), P(dw2), P(db2), P(wsc), nsc, B, Ci, Co, n, k,
+                                      None) == 0
     torch.cuda.synchronize()
+    assert torch.equal(dw, dw2) and torch.equal(db, db2)
     assert _rel(y.cpu().numpy(), S.conv3d(x, wq, b)) < 1e-5
     assert _rel(dx.cpu().numpy(), S.conv3d_dgrad(dy, wq)) < 1e-5
     gw, gb = S.conv3d_wgrad(x, dy, k)
@@ -131,12 +143,19 @@ def test_network_gradients_match_oracle(lib):
 
 
 def test_trained_network_warm_start_saves_iterations(lib):
-    """Train on 240 pairs at 32^3 (x8 mirror images) labelled by 60 plain iterations.  On 8
-    held-out pairs: the prediction is closer to the plain field than v = 0, and the warm start
-    (prediction smoothed by gamma^2 K, scale judged by the energy, v = 0 among the candidates)
-    reaches the energy of 60 plain iterations in fewer iterations on most pairs (the median; a
-    pair whose start falls in a basin of higher regulariser energy can miss the target within
-    the 120-iteration cap, and training with atomics changes which pairs do from run to run)."""
+    """Train on 240 pairs at 32^3 (x8 mirror images) labelled by 60 plain iterations; training is
+    deterministic (fixed-order weight-gradient sums).  On 8 held-out pairs, with backtracking in
+    every run so that accepted energies never rise:
+    * the prediction is closer to the plain field than v = 0;
+    * the warm start (prediction smoothed by gamma^2 K, scale chosen by the energy among
+      candidates that include the plain start v = 0) never starts above the plain start, by
+      construction, and in practice far below it;
+    * ten warm iterations are worth more than twenty plain ones on every pair: plain LDDMM needs
+      more than 20 iterations to reach the energy that the warm start reaches within 10.
+    The comparison is made at the warm run's energy rather than at a fixed plain target because
+    Beg's direction is not the exact gradient of the discrete energy: near a minimum it stops
+    being a descent direction, backtracking then shrinks the step to nothing, and plain and warm
+    runs come to rest at energies that differ by up to about 2% either way."""
     from paper_1605_02060_gb300 import surrogate as SG
     n, T, iters = 32, 10, 60
     train_pairs = SG.make_pairs(240, n, seed0=1000, amp_max=4.0)
@@ -146,18 +165,23 @@ def test_trained_network_warm_start_saves_iterations(lib):
     net = SG.UNet3D(n=n, batch=8, seed=0, out_scale=scale)
     hist = SG.train(net, X, Y, epochs=6, lr=1e-3)
     assert hist[-1] < 0.5 * hist[0], hist
-    warm, rels, cs = [], [], []
+    rels, start_ratio, k_plain, cs = [], [], [], []
     for pr in SG.make_pairs(8, n, seed0=5000, amp_max=4.0):
         v, _, _, _ = SG.run_plain(pr, iters, T)
         pred = SG.warm_start_field(net, pr, T)
         rels.append(_rel(pred, v.cpu().numpy()))
-        # target and warm run with backtracking: their energies never rise
-        _, E, _, _ = SG.run_plain(pr, iters, T, flags=1)
-        itw, c, nev, _ = SG.run_warm(net, pr, E[-1], 2 * iters, T, flags=1)
-        warm.append(itw)
+        _, Ep, _, _ = SG.run_plain(pr, 2 * iters, T, flags=1)      # Ep[k]: E(v_k), v_0 = 0
+        _, c, _, _ = SG.run_warm(net, pr, -np.inf, 10, T, flags=1)
+        Ew = SG.run_warm.last_energies                              # start, then 10 iterations
+        assert len(Ew) == 11
+        start_ratio.append(Ew[0] / Ep[0])
+        reach = [k for k, e in enumerate(Ep) if e <= Ew[-1]]
+        k_plain.append(reach[0] if reach else len(Ep))
         cs.append(c)
-    print("\nheld-out prediction rel-L2 %s; chosen scales %s; warm iterations to the plain energy "
-          "after %d: %s (mean %.1f)" % (np.round(rels, 3), cs, iters, warm, np.mean(warm)))
+    print("\nheld-out prediction rel-L2 %s; chosen scales %s; start energy / plain start %s; plain "
+          "iterations to the energy reached within 10 warm iterations: %s" %
+          (np.round(rels, 3), cs, np.round(start_ratio, 3), k_plain))
     assert np.mean(rels) < 0.9
-    assert np.median(warm) < 0.5 * iters, warm
-    assert sum(w < iters for w in warm) >= len(warm) // 2, warm
+    assert max(start_ratio) <= 1.0
+    assert np.median(start_ratio) < 0.3, start_ratio
+    assert min(k_plain) > 20, k_plain
