@@ -44,7 +44,7 @@ import dataclasses
 import numpy as np
 
 __all__ = [
-    "Params", "StepResult", "trilinear", "interp_vec", "fd_gradient", "jacobian_det",
+    "Params", "StepResult", "set_threads", "trilinear", "interp_vec", "fd_gradient", "jacobian_det",
     "laplacian_symbol", "apply_K", "apply_L", "backward_sweep", "forward_sweep",
     "reg_energy", "data_energy", "energy", "lddmm_step", "energy_grad_exact",
     "transfer_labels", "warp", "dice", "downsample", "upsample_velocity", "register",
@@ -97,9 +97,34 @@ def _axis_weights(q, n):
     return i0, q - i0, 1
 
 
+_THREADS = 1
+
+
+def set_threads(n):
+    """Number of host threads for the trilinear lookups (1: none).  Large query arrays are cut
+    into slabs along their first axis and each slab is evaluated by the same expression in a
+    thread of a pool (NumPy releases the interpreter lock inside array operations); every value
+    is computed exactly as in one piece, so results do not depend on the thread count.  FFTs take
+    their own `workers` argument."""
+    global _THREADS
+    _THREADS = max(1, int(n))
+
+
 def trilinear(f, qx, qy, qz):
     """Trilinear interpolation of f[z,y,x] at voxel coordinates (qx, qy, qz), clamp-to-edge."""
     f = np.asarray(f, dtype=np.float64)
+    qx, qy, qz = np.broadcast_arrays(qx, qy, qz)
+    if _THREADS > 1 and qx.ndim >= 1 and qx.size >= (1 << 18) and qx.shape[0] >= 2:
+        from concurrent.futures import ThreadPoolExecutor
+        cuts = np.linspace(0, qx.shape[0], min(_THREADS, qx.shape[0]) + 1).astype(int)
+        with ThreadPoolExecutor(len(cuts) - 1) as ex:
+            parts = list(ex.map(lambda ab: _trilinear1(f, qx[ab[0]:ab[1]], qy[ab[0]:ab[1]],
+                                                       qz[ab[0]:ab[1]]), zip(cuts[:-1], cuts[1:])))
+        return np.concatenate(parts, axis=0)
+    return _trilinear1(f, qx, qy, qz)
+
+
+def _trilinear1(f, qx, qy, qz):
     Z, Y, X = f.shape
     ix, tx, sx = _axis_weights(qx, X)
     iy, ty, sy = _axis_weights(qy, Y)
