@@ -28,9 +28,16 @@
  * destination buffers it is given.  The context owns its device buffers until lddmm_destroy.
  * Work is enqueued on the context's stream; a call that returns scalars or writes host memory
  * waits for that stream (bounded wait: LDDMM_ERR_TIMEOUT after params.timeout_s seconds).
- * Errors: a negative status; lddmm_last_error() describes the last failure of that context.
+ * Errors: a negative status; lddmm_last_error(ctx) describes the last failure of that context,
+ * and lddmm_last_error(NULL) the last failure on the calling thread of a call without one.
  * No exception crosses this interface.  After LDDMM_ERR_CUDA the context must be destroyed;
  * after any other error it stays usable.  One context may be used by one host thread at a time.
+ * LDDMM_ERR_TIMEOUT also reports a bounded wait inside a tensor-core pass that gave up: the
+ * kernel drains its copies and returns, that iteration's v is not valid, and the context stays
+ * usable once v is set again.
+ * Test hooks, read from the environment by lddmm_create (unset in normal use):
+ *   LDDMM_TEST_FAIL_ALLOC=k   the k-th device allocation of that call fails as out of memory;
+ *   LDDMM_TEST_POLL_LIMIT=n   each pipeline wait of the pre-split DFT pass gives up after n probes.
  */
 #ifndef LDDMM_H
 #define LDDMM_H
@@ -231,14 +238,19 @@ int lddmm_profile_stop(lddmm_ctx* ctx, lddmm_kernel_stat* out, int max_out, int*
 /* The paper has no counterpart of this entry point.  dst = K src (K = (gamma - alpha Lap_h)^-2,
  * FP32 per-axis real-DFT products, the same arithmetic as lddmm_apply_K with LDDMM_K_FP32) for
  * one scalar field of nx*ny*nz float32 on a grid of spacing (hx, hy, hz), enqueued on `stream`
- * (NULL = legacy default stream), WITHOUT allocating: for callers that cannot call cudaMalloc
- * (inside stream capture, host callbacks, processes whose memory is reserved by another pool).
- * Scratch is one file-scope device array (~11.5 MB, held by every GPU that loads the library until
- * exit).  Limits: nx*ny*nz <= 2^21, each axis in [2, 512]; larger grids give
- * LDDMM_ERR_INVALID_ARG.  src and dst must be device pointers (LDDMM_ERR_INVALID_ARG otherwise);
- * dst may equal src.  All calls share the array: calls that overlap on the GPU race, so issue them
- * on one stream.  The first call on a device looks up the array's address with that device
- * current; make it before any stream capture.  Returns LDDMM_ERR_CUDA on a CUDA failure. */
+ * (NULL = legacy default stream), WITHOUT allocating any memory.  It serves callers that cannot
+ * call cudaMalloc: a host callback, a real-time loop that must not stall on the allocator, a
+ * process whose GPU memory another framework's pool has reserved up front.  Its scratch (the
+ * intermediate field and the DFT tables) is one file-scope __device__ array of ~11.5 MB, which
+ * every GPU that loads the library holds until the process exits.  Limits: nx*ny*nz <= 2^21,
+ * each axis in [2, 512]; larger grids give LDDMM_ERR_INVALID_ARG.  src and dst must be device
+ * pointers (LDDMM_ERR_INVALID_ARG otherwise); dst may equal src.  The first call on a device
+ * looks up the array's device address with that device current; make it before any stream
+ * capture.  The tables are generated on the device, and again only when (n, h) of an axis
+ * changes; everything else in the array is rewritten before it is read, so nothing needs to
+ * start at zero.  All calls share the array: calls that overlap on the GPU (other streams, other
+ * host threads) race, so issue them on one stream.  LDDMM_ERR_CUDA on a CUDA failure; the reason
+ * of any failure is in lddmm_last_error(NULL) on the calling thread. */
 int lddmm_apply_K_noalloc(const float* src, float* dst, int nx, int ny, int nz, float hx,
                           float hy, float hz, float alpha, float gamma, void* stream);
 

@@ -150,6 +150,8 @@ struct KPlan {
   uint16_t* ks[3][2];
   float* kstail[2];
   int* err;  // device flag set by a tensor-core kernel whose bounded wait timed out
+  // probes per pipeline wait in the pre-split tensor-core pass (0: the default, 2^22)
+  uint32_t poll_limit;
 };
 // Build device tables for one grid (allocates; free with kplan_destroy).
 cudaError_t kplan_create(KPlan* kp, int nx, int ny, int nz, float hx, float hy, float hz,

@@ -63,6 +63,7 @@ struct KsArgs {
   float alpha, gamma;
   int X, Y;            // symbol: line l = (c X + x) Y + y
   int* err;
+  uint32_t poll;       // probes per pipeline wait before the CTA aborts
 };
 
 __host__ __device__ inline int ks_abytes(int split) { return (split ? 2 : 1) * KS_ABOX; }
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
         const int line0 = (blockIdx.x + i * gridDim.x) * 128;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = (int)(g % AS);
-          if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_aempty[s]), ((g / AS) & 1) ^ 1, abort)) goto p_done;
+          if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_aempty[s]), ((g / AS) & 1) ^ 1, abort, a.poll)) goto p_done;
           const uint32_t fa = ptx::smem_u32(&b_afull[s]);
           ptx::mbar_arrive_expect_tx(fa, (uint32_t)abytes);
           for (int pl = 0; pl < np; ++pl)
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
                              line0, pl, fa);
           if (!a.bres) {
             const int sb = (int)(gb % BS);
-            if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bempty[sb]), ((gb / BS) & 1) ^ 1, abort)) { ++g; goto p_done; }
+            if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bempty[sb]), ((gb / BS) & 1) ^ 1, abort, a.poll)) { ++g; goto p_done; }
             const uint32_t fb = ptx::smem_u32(&b_bfull[sb]);
             ptx::mbar_arrive_expect_tx(fb, (uint32_t)bbytes);
             for (int pl = 0; pl < np; ++pl)
@@ -332,19 +333,19 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
       const uint32_t blo = (uint32_t)a.Nc * 128u;               // B lo plane offset
       uint32_t g = 0;
       if (a.bres && my_tiles > 0 &&
-          !ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bfull[0]), 0u, abort)) goto m_done;
+          !ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bfull[0]), 0u, abort, a.poll)) goto m_done;
       for (int i = 0; i < my_tiles; ++i) {
         const int ab = i & 1;
         const uint32_t use = (uint32_t)(i >> 1);
-        if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tempty[ab]), (use & 1) ^ 1, abort)) break;
+        if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tempty[ab]), (use & 1) ^ 1, abort, a.poll)) break;
         ptx::tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(ab * a.Nc);
         bool ok = true;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = (int)(g % AS);
           const int sb = a.bres ? kb : (int)(g % BS);
-          if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_afull[s]), (g / AS) & 1, abort) ||
-              (!a.bres && !ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bfull[sb]), (g / BS) & 1, abort))) {
+          if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_afull[s]), (g / AS) & 1, abort, a.poll) ||
+              (!a.bres && !ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bfull[sb]), (g / BS) & 1, abort, a.poll))) {
             ok = false;
             break;
           }
@@ -391,7 +392,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
         for (int j = 0; j < 8; ++j) acc[j] = 0.f;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = (int)(g % AS);
-          if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_afull[s]), (g / AS) & 1, abort)) { ok = false; break; }
+          if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_afull[s]), (g / AS) & 1, abort, a.poll)) { ok = false; break; }
           // row m of the swizzled box: 16-byte chunk c (8 k values) stored at chunk c ^ (m % 8)
           const uint8_t* hrow = aring + s * abytes + m * 128;
           for (int c = 0; c < 8; ++c) {
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
         load_old_rows(o, lane, line0, a.nlines, cbeg * 16, ncols, oldv);
         if (cbeg + 1 < cend) load_old_rows(o, lane, line0, a.nlines, cbeg * 16 + 16, ncols, oldv + 4);
       }
-      if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tfull[ab]), use & 1, abort)) break;
+      if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tfull[ab]), use & 1, abort, a.poll)) break;
       ptx::tc_fence_after();
       const uint32_t trow = tmem + (uint32_t)(ab * a.Nc) + ((uint32_t)(q * 32) << 16);
       for (int cp = cbeg; cp < cend; cp += 2) {
@@ -580,6 +581,7 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
   a.alpha = kp.alpha; a.gamma = kp.gamma;
   a.X = kp.nx; a.Y = kp.ny;
   a.err = kp.err;
+  a.poll = kp.poll_limit ? kp.poll_limit : (1u << 22);
   const int P = ks_pitch(a.L);
   const int np = split ? 2 : 1;
   // A: [2 planes][nlines][P] bf16, box 64 k x 128 lines, 128-byte swizzle; k >= L and lines

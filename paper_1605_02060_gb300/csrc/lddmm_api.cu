@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -180,9 +181,23 @@ int validate(const lddmm_params* p, std::string& why) {
   return LDDMM_OK;
 }
 
+// Test hook (environment LDDMM_TEST_FAIL_ALLOC=k, read by lddmm_create): the k-th device
+// allocation of that create call fails as if the device were out of memory, so that the
+// clean-up path can be checked without exhausting a GPU.  0 or unset: no injection.
+thread_local int g_fail_alloc_countdown = 0;
+
 template <typename T>
 cudaError_t dalloc(T** p, int64_t n) {
+  if (g_fail_alloc_countdown > 0 && --g_fail_alloc_countdown == 0) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
   return cudaMalloc((void**)p, (size_t)n * sizeof(T));
+}
+
+int env_int(const char* name) {
+  const char* v = std::getenv(name);
+  return v ? std::atoi(v) : 0;
 }
 
 const float* field_src(lddmm_ctx* ctx, const float* user, int64_t n, float* stage, int* rc) {
@@ -287,8 +302,15 @@ int read_energy(lddmm_ctx* ctx, lddmm_energy* out, bool with_det) {
                      ctx->stream));
   int rc = wait_stream(ctx);
   if (rc) return rc;
-  if (ctx->acc_host->nonfinite)
-    return fail(ctx, LDDMM_ERR_CUDA, "a tensor-core pipeline wait timed out (results invalid)");
+  if (ctx->acc_host->nonfinite) {
+    // a bounded wait inside a tensor-core pass gave up: that pass's output (and so v) is not
+    // valid.  The kernel drained its copies and freed its resources, so the context stays
+    // usable once the flag is cleared.
+    CK(cudaMemsetAsync(L.kp.err, 0, sizeof(int), ctx->stream));
+    return fail(ctx, LDDMM_ERR_TIMEOUT,
+                "a tensor-core pipeline wait on the GPU gave up: this iteration's result is invalid "
+                "(set the velocity again)");
+  }
   const double h3 = (double)L.hx * L.hy * L.hz;
   const double s = ctx->p.sigma;
   out->reg = ctx->acc_host->e_reg * h3 / (double)ctx->p.T;
@@ -464,6 +486,11 @@ int do_step(lddmm_ctx* ctx, lddmm_energy* out) {
 
 }  // namespace
 
+namespace lddmm {
+// The message lddmm_last_error(NULL) returns on this thread (entry points without a context).
+void set_context_free_error(const char* msg) { g_global_error = msg; }
+}  // namespace lddmm
+
 extern "C" {
 
 int lddmm_default_params(lddmm_params* p, int nx, int ny, int nz) {
@@ -493,6 +520,10 @@ int lddmm_create(const lddmm_params* p, const float* I0, const float* I1, const 
   if (!I0 || !I1) return fail(nullptr, LDDMM_ERR_INVALID_ARG, "I0 and I1 are required");
   lddmm_ctx* ctx = new (std::nothrow) lddmm_ctx();
   if (!ctx) return fail(nullptr, LDDMM_ERR_OOM, "host allocation failed");
+  g_fail_alloc_countdown = env_int("LDDMM_TEST_FAIL_ALLOC");
+  // Test hook (environment LDDMM_TEST_POLL_LIMIT=n): each pipeline wait of the pre-split
+  // tensor-core pass gives up after n probes, so that the abort path can be exercised.
+  const int poll_limit = env_int("LDDMM_TEST_POLL_LIMIT");
   ctx->p = *p;
   ctx->eps = p->epsilon;
   ctx->st = p->storage;
@@ -545,6 +576,7 @@ int lddmm_create(const lddmm_params* p, const float* I0, const float* I1, const 
     ok = A(dalloc(&L.I0, ie)) && A(dalloc(&L.I1, ie)) && A(dalloc(&L.M, ie)) &&
          A(dalloc(&L.IM, 2 * ie)) &&
          A(kplan_create(&L.kp, L.g.nx, L.g.ny, L.g.nz, L.hx, L.hy, L.hz, p->alpha, p->gamma));
+    L.kp.poll_limit = poll_limit > 0 ? (uint32_t)poll_limit : 0u;
   }
   const int64_t ve = (T * 3 * N * (int64_t)ctx->es + 3) / 4;  // velocity storage, in floats
   ok = ok && A(dalloc(&ctx->v, ve)) && A(dalloc(&ctx->v_tmp, ve)) &&
@@ -555,6 +587,7 @@ int lddmm_create(const lddmm_params* p, const float* I0, const float* I1, const 
        A(dalloc(&ctx->acc, 1)) && A(dalloc(&ctx->flag, 1)) && A(dalloc(&ctx->hist, 3 * 65536)) &&
        A(cudaMallocHost((void**)&ctx->acc_host, sizeof(Acc)));
   if (ok && (p->flags & 1)) ok = A(dalloc(&ctx->v_prev, ve));
+  g_fail_alloc_countdown = 0;
   if (!ok) return bail(LDDMM_ERR_OOM);
   if (cudaMemsetAsync(ctx->v, 0, (size_t)ve * sizeof(float), ctx->stream) != cudaSuccess) {
     ctx->err = "memset failed";

@@ -58,10 +58,12 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait that also gives up as soon as *abort is set by another role of the CTA.
+// Bounded wait that also gives up as soon as *abort is set by another role of the CTA, or after
+// `limit` probes (default 2^22, seconds; a test sets a tiny limit to exercise the abort path).
 __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity,
-                                                   volatile int* abort) {
-  for (uint32_t it = 0; it < (1u << 22); ++it) {
+                                                   volatile int* abort,
+                                                   uint32_t limit = 1u << 22) {
+  for (uint32_t it = 0; it < limit; ++it) {
     if (mbar_try(bar, parity)) return true;
     if ((it & 15) == 15 && *abort) return false;
   }
