@@ -10,7 +10,8 @@ mask pair at 264x160x228 (seeded), resident in HBM before the timed region; the 
 
 N > 1 (torchrun): N independent replicas, one per GPU (registrations do not exchange data);
 value = iterations of all ranks / max-over-ranks time.  --impl reference times the FP64 CPU
-oracle on a bounded sample of the same workload.
+oracle on all host cores: each step is one full T = 10 iteration on the same brain at
+132x80x114 (1/8 of the voxels), and the rate is scaled to 264x160x228 by the voxel count.
 """
 from __future__ import annotations
 
@@ -179,47 +180,75 @@ def make_inputs(seed=1):
     return make_inputs_full(seed)[0]
 
 
-def oracle_sample_rate(pair, frac_z, frac_y=1.0, frac_x=1.0):
-    """Time one T=1 iteration of the FP64 oracle on the central crop of the workload and scale
-    to iterations/s of the full T=10 workload (work is linear in voxels and in T)."""
+SAMPLE_SHAPE = (114, 80, 132)      # the same brain on the 100 um grid: half of each axis
+
+
+def _oracle_threads():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def oracle_iteration(threads):
+    """Seconds of one full iteration (T = 10, all time steps, K by FFT) of the FP64 oracle on the
+    brain pair at 132x80x114 (the same brain at the 100 um grid, 1/8 of the benchmark's voxels),
+    with its trilinear lookups on `threads` host threads and scipy FFT workers.  The oracle's work
+    is linear in the voxel count, so the rate at 264x160x228 is 1 / (8 x seconds)."""
     import numpy as np
 
     from oracle import lddmm as O
-    Z, Y, X = SHAPE
-    cz, cy, cx = int(round(Z * frac_z)), int(round(Y * frac_y)), int(round(X * frac_x))
-    z0, y0, x0 = (Z - cz) // 2, (Y - cy) // 2, (X - cx) // 2
-    sl = (slice(z0, z0 + cz), slice(y0, y0 + cy), slice(x0, x0 + cx))
-    I0, I1, M = pair.I0[sl], pair.I1[sl], pair.M[sl]
-    v = np.zeros((1, 3) + I0.shape)
+    from paper_1605_02060_gb300 import synth
+    if "sample" not in _INPUTS:
+        _INPUTS["sample"] = synth.brain_pair(shape=SAMPLE_SHAPE, base_shape=BASE, seed=1)[0]
+    pair = _INPUTS["sample"]
+    O.set_threads(threads)
+    v = np.zeros((T, 3) + SAMPLE_SHAPE)
     t0 = time.perf_counter()
-    O.lddmm_step(v, I0, I1, M, O.Params(T=1))
-    dt = time.perf_counter() - t0
-    scale = (Z * Y * X) / float(cz * cy * cx) * T
-    return 1.0 / (dt * scale), dt, "%dx%dx%d crop, T=1 (1/%.0f of one iteration)" % (cx, cy, cz, scale)
+    O.lddmm_step(v, pair.I0, pair.I1, pair.M, O.Params(T=T), workers=threads)
+    return time.perf_counter() - t0
+
+
+def _sample_scale():
+    return (SHAPE[0] * SHAPE[1] * SHAPE[2]) / float(SAMPLE_SHAPE[0] * SAMPLE_SHAPE[1] * SAMPLE_SHAPE[2])
+
+
+def _sample_text(threads):
+    return ("one full T=10 iteration per step on the same brain at %dx%dx%d (1/%.0f of the "
+            "voxels), rate scaled by the voxel count; NumPy/SciPy FP64, trilinear lookups on %d "
+            "threads, scipy.fft workers=%d" % (SAMPLE_SHAPE[2], SAMPLE_SHAPE[1], SAMPLE_SHAPE[0],
+                                                _sample_scale(), threads, threads))
 
 
 def run_reference(args):
     ws, rank, _ = dist_setup(args)
     if rank != 0:
         return 0
-    pair = make_inputs()
-    rates = []
+    threads = _oracle_threads()
+    secs = []
     for i in range(args.warmup + args.steps):
-        r, dt, sample = oracle_sample_rate(pair, 0.5, 0.5, 0.5)
+        dt = oracle_iteration(threads)
         if i >= args.warmup:
-            rates.append(r)
-    value = statistics.mean(rates)
+            secs.append(dt)
+    per_step = sum(secs) / len(secs)
+    value = 1.0 / (per_step * _sample_scale())
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "masked LDDMM %dx%dx%d T=10, brain-shaped atlas/target mask pair "
-                                             "(seed 1)" % (SHAPE[2], SHAPE[1], SHAPE[0]),
-                                 "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample + " per step; NumPy/SciPy FP64, one thread"},
+            "data": "synthetic", "config": workload_config(args.kmode, ws),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": _sample_text(threads)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def workload_config(kmode, ws=1):
+    Z, Y, X = SHAPE
+    N = X * Y * Z
+    kname = {0: "fp32", 1: "bf16x3", 2: "bf16"}[kmode]
+    return {"workload": "masked LDDMM %dx%dx%d T=10, brain-shaped atlas/target mask pair (seed 1), "
+                        "fp32 fields, K via %s DFT products" % (X, Y, Z, kname),
+            "grid": [X, Y, Z], "T": T, "alpha": 0.02, "gamma": 1.0, "sigma": 0.1,
+            "epsilon": 1e-3, "k_mode": kname, "parallelism": "replicas" if ws > 1 else "single",
+            "l2": "working set %.1f GB > L2 (no flush)" % ((2 * T * 3 + 2 * T + 20) * N * 4 / 1e9)}
 
 
 def run_ours(args):
@@ -329,25 +358,18 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": traffic, "kernel": name,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz,
                 "launch_time": LAUNCH_TIME}
-    # CPU baseline: the oracle, one thread, on half the grid at T=1
+    # CPU baseline: the oracle on all host cores, one full T = 10 iteration at 132x80x114
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        r, dt, sample = oracle_sample_rate(pair, 0.5)
-        cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": sample + "; NumPy/SciPy FP64, one thread; %.1f s" % dt}
-    kname = {0: "fp32", 1: "bf16x3", 2: "bf16"}[args.kmode]
+        threads = _oracle_threads()
+        dt = oracle_iteration(threads)
+        cpu = {"value": 1.0 / (dt * _sample_scale()), "unit": UNIT, "cores": threads,
+               "kind": "oracle", "sample": _sample_text(threads) + "; %.1f s" % dt}
+    cfg = workload_config(args.kmode, ws)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": "masked LDDMM %dx%dx%d T=10, brain-shaped atlas/target mask "
-                                   "pair (seed 1), fp32 fields, K via %s DFT products"
-                                   % (X, Y, Z, kname),
-                       "grid": [X, Y, Z], "T": T, "alpha": 0.02, "gamma": 1.0, "sigma": 0.1,
-                       "epsilon": 1e-3, "k_mode": kname,
-                       "parallelism": "replicas" if ws > 1 else "single",
-                       "l2": "working set %.1f GB > L2 (no flush)" % (
-                           (2 * T * 3 + 2 * T + 20) * N * 4 / 1e9)},
+            "data": "synthetic", "config": cfg,
             "clocks": clk, "e2e": e2e, "gpu_launches": int(sum(v[0] for v in prof.values())),
             "profiled_ms_per_step": ms_prof / args.steps,
             "roofline": roof, "cpu_baseline": cpu,
@@ -565,10 +587,11 @@ def main():
                     help="override the 264 160 228 grid (tests only; the metric is quoted on the "
                          "default)")
     args = ap.parse_args()
-    global SHAPE, METRIC
+    global SHAPE, METRIC, SAMPLE_SHAPE
     if args.grid:
         X, Y, Z = args.grid
         SHAPE = (Z, Y, X)
+        SAMPLE_SHAPE = tuple((n + 1) // 2 for n in SHAPE)
         METRIC = "LDDMM iters/s at %dx%dx%d T=10" % (X, Y, Z)
     if args.kmode is None:
         args.kmode = DEFAULT_KMODE
