@@ -137,12 +137,6 @@ struct KPlan {
   // tensor-core operand tables per axis (x, y, z) and direction (0 forward, 1 inverse):
   // nk = Npad/16 k-steps, each [hi | lo] bf16 blocks of Npad x 16 in K-major core-matrix order
   uint16_t* tc[3][2];
-  // x axis with 256 < nx <= 264 (the TMA pass): the first 256 output columns on the tensor
-  // cores (tables as above with 256 rows), the last xtw = nx - 256 columns in FP32 on the CUDA
-  // cores from xtail[dir] = B(k, 256 + j) as float [Kpad][8] (zero beyond nx)
-  uint16_t* tcx[2];
-  float* xtail[2];
-  int xtw;
   // operand tables of the pre-split pass (kernels_ks.cu) per axis and direction: bf16
   // [2][Nc][Kp] (hi plane, lo plane), row n = output column (Nc = min(256, ceil16(n))), k
   // contiguous (Kp = ceil16(n)), zero beyond the axis length; for 256 < nx <= 264 the x
@@ -167,10 +161,6 @@ cudaError_t apply_K(const KPlan& kp, int mode, const float* in, float* out, floa
                     int ncomp, cudaStream_t s, const Hook& hook = Hook(),
                     float* v_upd = nullptr, float eps = 0.f, long long cap = 0,
                     bool in_split = false);
-// Persistent warp-specialised TMA/tcgen05 pass (kernels_tma.cu) and its shape condition.
-bool tma_pass_supported(const KPlan& kp, int axis);
-cudaError_t tma_axis_pass(const KPlan& kp, int axis, bool inverse, int split, const float* in,
-                          float* out, int ncomp, int epi, float eps, cudaStream_t s);
 // Output addressing of a pre-split pass: line l = (a D + b) E + e is written at column n to
 // element (a F + b) P + e + n G, as bf16 hi/lo planes `plane` elements apart (KS_OUT_SPLIT), as
 // fp32 (KS_OUT_F32), or as the update out <- out - eps (2 out - C) of fp32 rows (KS_OUT_UPD);

@@ -110,17 +110,6 @@ static void ks_tail_table(const std::vector<float>& R, int n, bool inverse, std:
     }
 }
 
-// FP32 tail columns 256..n-1 of B as [Kpad][8] (zero beyond n and for j >= n - 256).
-static void tail_table(const std::vector<float>& R, int n, bool inverse, std::vector<float>& t) {
-  const int Kpad = (n + 15) / 16 * 16;
-  t.assign((size_t)Kpad * 8, 0.f);
-  for (int k = 0; k < n; ++k)
-    for (int j = 0; j < 8 && 256 + j < n; ++j) {
-      const int col = 256 + j;
-      t[(size_t)k * 8 + j] = inverse ? R[(size_t)k * n + col] : R[(size_t)col * n + k];
-    }
-}
-
 template <typename T>
 static cudaError_t upload(T** dst, const std::vector<T>& src) {
   cudaError_t e = cudaMalloc((void**)dst, src.size() * sizeof(T));
@@ -160,17 +149,6 @@ cudaError_t kplan_create(KPlan* kp, int nx, int ny, int nz, float hx, float hy, 
         }
       }
     }
-    if (d == 0 && nx > 256 && nx <= 264) {
-      kp->xtw = nx - 256;
-      for (int dir = 0; dir < 2; ++dir) {
-        std::vector<uint16_t> t;
-        tc_table(R, nx, dir == 1, 256, t);
-        if ((e = upload(&kp->tcx[dir], t)) != cudaSuccess) return e;
-        std::vector<float> tt;
-        tail_table(R, nx, dir == 1, tt);
-        if ((e = upload(&kp->xtail[dir], tt)) != cudaSuccess) return e;
-      }
-    }
   }
   cudaError_t e = cudaMalloc((void**)&kp->err, sizeof(int));
   if (e != cudaSuccess) return e;
@@ -185,8 +163,6 @@ void kplan_destroy(KPlan* kp) {
     for (int dir = 0; dir < 2; ++dir)
       if (kp->tc[d][dir]) cudaFree(kp->tc[d][dir]);
   for (int dir = 0; dir < 2; ++dir) {
-    if (kp->tcx[dir]) cudaFree(kp->tcx[dir]);
-    if (kp->xtail[dir]) cudaFree(kp->xtail[dir]);
     for (int d = 0; d < 3; ++d)
       if (kp->ks[d][dir]) cudaFree(kp->ks[d][dir]);
     if (kp->kstail[dir]) cudaFree(kp->kstail[dir]);
@@ -408,9 +384,7 @@ static cudaError_t apply_K_tc(const KPlan& kp, int split, const float* in, float
 #define TC_PASS(kid, axis, inv, src, dst, epi)                                         \
   do {                                                                                 \
     hook(kid, 0);                                                                      \
-    e = tma_pass_supported(kp, axis)                                                   \
-            ? tma_axis_pass(kp, axis, inv, split, src, dst, ncomp, epi, eps, s)        \
-            : tc_axis_pass(kp, axis, inv, split, src, dst, ncomp, epi, eps, s);        \
+    e = tc_axis_pass(kp, axis, inv, split, src, dst, ncomp, epi, eps, s);              \
     hook(kid, 1);                                                                      \
     if (e != cudaSuccess) return e;                                                    \
   } while (0)

@@ -513,6 +513,23 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
 
 int g_ks_sms = 0;
 
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
 // fp32 rows [nrows][L] -> split field: one thread per (row, column), columns fastest.
 __global__ void k_split_rows(const float* __restrict__ in, long long nrows, int L, int split,
                              KsOut o) {
@@ -529,6 +546,8 @@ __global__ void k_split_rows(const float* __restrict__ in, long long nrows, int 
 }
 
 }  // namespace
+
+void* tma_encode_fn() { return reinterpret_cast<void*>(encode_fn()); }
 
 int ks_pitch(int L) { return (L + 7) / 8 * 8; }
 

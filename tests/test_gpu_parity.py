@@ -136,6 +136,30 @@ def test_K_tensor_modes_full_size_deterministic(L):
     assert float((res[2] - ref).norm() / ref.norm()) < 1e-2
 
 
+@pytest.mark.parametrize("shape", [(40, 260, 300), (258, 12, 36), (20, 24, 270)])
+def test_K_outside_the_pre_split_path_deterministic_and_matches_oracle(L, O, shape):
+    """Axes longer than the pre-split pass takes (x > 264, y or z > 256): the fp32-input
+    tensor-core pass.  Each tensor-core mode repeats bit for bit and matches the oracle (bf16x3
+    2e-5, plain bf16 1e-2)."""
+    Z, Y, X = shape
+    rng = np.random.default_rng(8)
+    f = rng.standard_normal(shape).astype(np.float32)
+    ref = O.apply_K(f, 0.02, 1.0, (1, 1, 1), workers=-1)
+    fd = _dev(f)
+    a = torch.zeros(shape, device="cuda")
+    for code, tol in ((1, 2e-5), (2, 1e-2)):
+        p = L.default_params(X, Y, Z, k_mode=code)
+        with L.Lddmm(p, a, a) as ctx:
+            outs = []
+            for _ in range(3):
+                out = torch.empty_like(fd)
+                ctx.apply_K(fd, out)
+                outs.append(out)
+            torch.cuda.synchronize()
+        assert all(torch.equal(outs[0], o) for o in outs[1:]), code
+        assert _rel(outs[0].cpu().numpy(), ref) < tol, code
+
+
 # --------------------------------------------------------------------------- one iteration
 
 def _pair_small(synth, shape=(32, 32, 32)):
