@@ -295,6 +295,18 @@ int lddmm_net_adam(float* w, const float* g, float* m, float* v, void* w_bf16, i
                    float lr, float beta1, float beta2, float eps, int step, void* stream);
 int lddmm_net_cast_bf16(const float* a, void* b, int64_t count, void* stream);
 
+/* Resampling between two grids over the same box (the warm start's coarse network grid and the
+ * registration grid; the paper has no counterpart): dst = trilinear interpolation of src at
+ * cell-centred coordinates q_d = (i_d + 0.5) s_d / d_d - 0.5 (source voxels, clamped to the
+ * source grid), for nfields fields [nfields][sz][sy][sx] -> [nfields][dz][dy][dx] (x fastest);
+ * field f is multiplied by (s0, s1, s2)[f % ncomp] (ncomp = 1 for scalar fields, 3 for vector
+ * fields [..][3][..] whose components change units with the grid).  Device pointers; src and
+ * dst must not overlap; enqueued on `stream`; LDDMM_ERR_INVALID_ARG on a bad shape. */
+int lddmm_resample(const float* src, int sx, int sy, int sz, float* dst, int dx, int dy, int dz,
+                   int nfields, int ncomp, float s0, float s1, float s2, void* stream);
+/* x <- c x for count floats of device memory, enqueued on `stream`. */
+int lddmm_scale(float* x, int64_t count, float c, void* stream);
+
 /* Change the bound on host waits for this context (seconds, <= 0: 600 s). */
 int lddmm_set_timeout(lddmm_ctx* ctx, float seconds);
 

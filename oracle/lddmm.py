@@ -47,7 +47,7 @@ __all__ = [
     "Params", "StepResult", "set_threads", "trilinear", "interp_vec", "fd_gradient", "jacobian_det",
     "laplacian_symbol", "apply_K", "apply_L", "backward_sweep", "forward_sweep",
     "reg_energy", "data_energy", "energy", "lddmm_step", "energy_grad_exact",
-    "transfer_labels", "warp", "dice", "downsample", "upsample_velocity", "register",
+    "transfer_labels", "warp", "dice", "downsample", "upsample_velocity", "resample", "register",
 ]
 
 
@@ -472,6 +472,19 @@ def upsample_velocity(v, fine_shape, f_coarse, f_fine):
         for e in range(3):
             out[j, e] = trilinear(v[j, e], qx, qy, qz)
     return out
+
+
+def resample(f, dst_shape):
+    """f sampled on another grid over the same box: trilinear interpolation at cell-centred
+    coordinates, q_d = (i_d + 0.5) s_d / d_d - 0.5 source voxels along each axis (clamped).  Used
+    by the warm start to move masks to the network's grid and velocities back; a velocity in
+    voxels of one grid becomes one in voxels of the other by the ratio of the sizes along its own
+    axis, which the caller applies."""
+    f = np.asarray(f, np.float64)
+    gz, gy, gx = _grid(dst_shape)
+    (sz, sy, sx), (dz, dy, dx) = f.shape, tuple(dst_shape)
+    return trilinear(f, (gx + 0.5) * sx / dx - 0.5, (gy + 0.5) * sy / dy - 0.5,
+                     (gz + 0.5) * sz / dz - 0.5)
 
 
 def register(I0, I1, M, p: Params, iterations, factors=(1,), v0=None, workers=None):

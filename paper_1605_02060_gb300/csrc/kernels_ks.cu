@@ -508,6 +508,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem, 512u);
   }
+  __syncthreads();   // abort_sh as the MMA warp left it
   if (threadIdx.x == 0 && abort_sh) atomicExch(a.err, 3);
 }
 

@@ -118,6 +118,9 @@ _SIGS = {
     "lddmm_net_adam": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_float,
                                       ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int, _P]),
     "lddmm_net_cast_bf16": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
+    "lddmm_resample": (ctypes.c_int, [_P] + [ctypes.c_int] * 3 + [_P] + [ctypes.c_int] * 5
+                       + [ctypes.c_float] * 3 + [_P]),
+    "lddmm_scale": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_float, _P]),
     "lddmm_last_error": (ctypes.c_char_p, [_P]),
     "lddmm_destroy": (None, [_P]),
 }
@@ -356,6 +359,28 @@ def histogram_match(I0, M0, I1, M1, out=None, bins=32, points=8):
                                       points, _ptr(out), _current_stream())
     _check(rc, None)
     return out
+
+
+def resample(src, dst_shape, ncomp=1, scale=(1.0, 1.0, 1.0), out=None):
+    """Trilinear resampling at cell-centred coordinates of device float32 fields
+    (..., sz, sy, sx) to (..., dz, dy, dx); field f scaled by scale[f % ncomp]."""
+    import torch
+    sz, sy, sx = src.shape[-3:]
+    dz, dy, dx = dst_shape
+    lead = tuple(src.shape[:-3])
+    nf = int(np.prod(lead)) if lead else 1
+    if out is None:
+        out = torch.empty(lead + (dz, dy, dx), dtype=torch.float32, device=src.device)
+    _check(load().lddmm_resample(_ptr(src), sx, sy, sz, _ptr(out), dx, dy, dz, nf, ncomp,
+                                 float(scale[0]), float(scale[1]), float(scale[2]),
+                                 _current_stream()), None)
+    return out
+
+
+def scale_(x, c):
+    """x <- c x in place (device float32 tensor)."""
+    _check(load().lddmm_scale(_ptr(x), x.numel(), float(c), _current_stream()), None)
+    return x
 
 
 def mask_morphology(I, threshold, r_open, r_close, out=None):

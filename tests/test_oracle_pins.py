@@ -612,3 +612,27 @@ def test_threaded_lookups_give_the_same_bits():
     for x, y in ((a.v_new, b.v_new), (a.u10, b.u10), (a.u01, b.u01), (a.J0T, b.J0T), (a.W, b.W)):
         np.testing.assert_array_equal(x, y)
     assert a.E_reg == b.E_reg and a.E_data == b.E_data
+
+
+def test_resample_between_grids_of_one_box():
+    """Cell-centred resampling: the identity on the same grid; a constant stays constant; an
+    affine function of the box coordinate (u = (i + 0.5) / n) is reproduced exactly wherever the
+    sample point lies inside the source grid, up and down and with different ratios per axis; a
+    2x coarsening of a field linear along x gives the mean of each pair."""
+    rng = _rng(31)
+    f = rng.standard_normal((5, 6, 7))
+    np.testing.assert_array_equal(O.resample(f, f.shape), f)
+    np.testing.assert_allclose(O.resample(np.full((4, 5, 6), 2.5), (9, 3, 13)), 2.5, rtol=1e-15)
+    for src, dst in (((6, 8, 10), (15, 11, 23)), ((20, 12, 16), (7, 5, 6))):
+        z, y, x = np.meshgrid(*[(np.arange(n) + 0.5) / n for n in src], indexing="ij")
+        g = 0.3 + 2.0 * x - 1.5 * y + 0.7 * z
+        out = O.resample(g, dst)
+        Z, Y, X = np.meshgrid(*[(np.arange(n) + 0.5) / n for n in dst], indexing="ij")
+        ref = 0.3 + 2.0 * X - 1.5 * Y + 0.7 * Z
+        # inside: every sample coordinate between the first and last source cell centre
+        ins = ((X >= 0.5 / src[2]) & (X <= 1 - 0.5 / src[2]) & (Y >= 0.5 / src[1]) &
+               (Y <= 1 - 0.5 / src[1]) & (Z >= 0.5 / src[0]) & (Z <= 1 - 0.5 / src[0]))
+        assert ins.sum() > 20
+        np.testing.assert_allclose(out[ins], ref[ins], rtol=0, atol=1e-12)
+    h = np.broadcast_to(np.arange(8.0), (4, 4, 8))
+    np.testing.assert_allclose(O.resample(h, (4, 4, 4))[0, 0], [0.5, 2.5, 4.5, 6.5], atol=1e-12)
