@@ -11,8 +11,10 @@
 //   conv_wgrad dw[co,ci,t] += sum_b sum_v dy[b,co,v] x[b,ci,v+o(t)],  db[co] += sum dy[b,co,v]
 //              (fixed-order partial sums in caller scratch: the same bits on every run)
 // plus 2x average pooling, 2x nearest upsampling, channel concatenation, ReLU backward, the MSE
-// loss and Adam.  Forward tiles: 8x8x4 output voxels x 16 output channels per block, input
-// channels staged 8 at a time with a one-voxel halo in shared memory.
+// loss and Adam.  Convolutions whose input channels come in groups of 16 run on the tensor cores
+// (kernels_conv_tc.cu); the others (the 2-channel network input, the 3-channel head gradient)
+// here: 8x8x4 output voxels x 16 output channels per block, input channels staged 8 at a time
+// with a one-voxel halo in shared memory.
 #include <cuda_bf16.h>
 
 #include "kernels.h"
@@ -349,8 +351,15 @@ static inline int gs(int64_t n) {
 
 static int tiles_of(int n) { return ((n + BX - 1) / BX) * ((n + BY - 1) / BY) * ((n + BZ - 1) / BZ); }
 
+bool conv_tc_supported(int Ci, int Co);
+cudaError_t conv_tc_fwd(const float* x, const void* w, const float* bias, float* y, int B, int Ci,
+                        int Co, int n, int ks, int relu, int accumulate, cudaStream_t s);
+
 cudaError_t net_conv_fwd(const float* x, const void* w, const float* bias, float* y, int B, int Ci,
                          int Co, int n, int ks, int relu, int accumulate, cudaStream_t s) {
+  // input channels in groups of 16: the tensor-core implicit GEMM (kernels_conv_tc.cu)
+  if (conv_tc_supported(Ci, Co))
+    return conv_tc_fwd(x, w, bias, y, B, Ci, Co, n, ks, relu, accumulate, s);
   dim3 grid(tiles_of(n), (Co + CT - 1) / CT, B);
   k_conv_fwd<<<grid, NTV, 0, s>>>(x, (const __nv_bfloat16*)w, bias, y, Ci, Co, n, ks, relu,
                                   accumulate);

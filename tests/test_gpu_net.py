@@ -34,8 +34,11 @@ def _bf(a):
     return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16)
 
 
-@pytest.mark.parametrize("B,Ci,Co,n,k", [(2, 5, 18, 8, 3), (1, 3, 4, 12, 3), (2, 16, 3, 8, 1),
-                                        (1, 9, 33, 4, 3)])
+@pytest.mark.parametrize("B,Ci,Co,n,k", [(2, 5, 18, 8, 3), (1, 3, 4, 12, 3), (1, 9, 33, 4, 3),
+                                        # input channels in groups of 16: tensor-core path
+                                        (2, 16, 3, 8, 1), (2, 16, 32, 8, 3), (1, 32, 16, 12, 3),
+                                        (2, 48, 16, 8, 3), (1, 128, 128, 8, 3), (1, 16, 33, 12, 3),
+                                        (2, 32, 30, 8, 1)])
 def test_conv_kernels_match_oracle(lib, B, Ci, Co, n, k):
     from oracle import surrogate as S
     rng = np.random.default_rng(0)
