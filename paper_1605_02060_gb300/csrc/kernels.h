@@ -163,9 +163,10 @@ cudaError_t apply_K(const KPlan& kp, int mode, const float* in, float* out, floa
                     bool in_split = false);
 // Output addressing of a pre-split pass: line l = (a D + b) E + e is written at column n to
 // element (a F + b) P + e + n G, as bf16 hi/lo planes `plane` elements apart (KS_OUT_SPLIT), as
-// fp32 (KS_OUT_F32), or as the update out <- out - eps (2 out - C) of fp32 rows (KS_OUT_UPD);
+// fp32 (KS_OUT_F32), or as the update out <- out - eps (2 out - C) of fp32 rows (KS_OUT_UPD) or
+// of bf16 rows (KS_OUT_UPD_BF16, arithmetic in FP32, one rounding);
 // sym: scale by the K symbol of the z-forward product.
-enum { KS_OUT_SPLIT = 0, KS_OUT_F32 = 1, KS_OUT_UPD = 2 };
+enum { KS_OUT_SPLIT = 0, KS_OUT_F32 = 1, KS_OUT_UPD = 2, KS_OUT_UPD_BF16 = 3 };
 struct KsOut {
   int kind;
   int sym;
@@ -185,6 +186,12 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
 // True when apply_K(kp, mode, ..., ncomp, cap) takes the pre-split path; its input may then be
 // given already split (in_split): bf16 hi/lo planes [ncomp][nz][ny][ks_pitch(nx)].
 bool ks_path(const KPlan& kp, int mode, int ncomp, long long cap);
+// The pre-split K of `in` (3 components, on the pre-split path only) with the update fused into
+// its last product for a velocity stored in bf16: v <- bf16(v - eps (2 v - K in)), the
+// arithmetic in FP32.  cudaErrorNotSupported when the pre-split path does not apply.
+cudaError_t apply_K_update_bf16(const KPlan& kp, int mode, const float* in, float* work,
+                                cudaStream_t s, const Hook& hook, void* v_bf16, float eps,
+                                long long cap, bool in_split);
 // fp32 rows [nrows][L] -> split field at the addresses `o` gives (line = row, column = n).
 cudaError_t ks_split_rows(const float* in, long long nrows, int L, int split, const KsOut& o,
                           cudaStream_t s);

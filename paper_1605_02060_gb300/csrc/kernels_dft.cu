@@ -322,7 +322,7 @@ static cudaError_t apply_K_fp32(const KPlan& kp, const float* in, float* out, fl
 // split into work; without the update the result then lands in work and is copied to out.
 static cudaError_t apply_K_ks(const KPlan& kp, int split, const float* in, float* out,
                               float* work, int ncomp, cudaStream_t s, const Hook& hook,
-                              float* v_upd, float eps, bool in_split) {
+                              void* v_upd, float eps, bool in_split, int upd_kind = KS_OUT_UPD) {
   const long long X = kp.nx, Y = kp.ny, Z = kp.nz, C = ncomp;
   const long long Px = ks_pitch(kp.nx), Py = ks_pitch(kp.ny), Pz = ks_pitch(kp.nz);
   cudaError_t e;
@@ -356,8 +356,8 @@ static cudaError_t apply_K_ks(const KPlan& kp, int split, const float* in, float
     src = ps[p].o.out;
   }
   // x inverse: from bA into v_upd (update) or fp32 rows
-  float* dst = v_upd ? v_upd : bB;
-  const KsOut o6{v_upd ? KS_OUT_UPD : KS_OUT_F32, 0, dst, 0, 1, 1, 1, X, 1};
+  void* dst = v_upd ? v_upd : (void*)bB;
+  const KsOut o6{v_upd ? upd_kind : KS_OUT_F32, 0, dst, 0, 1, 1, 1, X, 1};
   hook(KID_KX_INV, 0);
   e = ks_axis_pass(kp, 0, true, split, src, C * Z * Y, o6, eps, s);
   hook(KID_KX_INV, 1);
@@ -365,6 +365,14 @@ static cudaError_t apply_K_ks(const KPlan& kp, int split, const float* in, float
   if (!v_upd && dst != out)
     e = cudaMemcpyAsync(out, dst, (size_t)C * X * Y * Z * sizeof(float), cudaMemcpyDeviceToDevice, s);
   return e;
+}
+
+cudaError_t apply_K_update_bf16(const KPlan& kp, int mode, const float* in, float* work,
+                                cudaStream_t s, const Hook& hook, void* v_bf16, float eps,
+                                long long cap, bool in_split) {
+  if (!ks_path(kp, mode, 3, cap)) return cudaErrorNotSupported;
+  return apply_K_ks(kp, mode == LDDMM_K_BF16X3 ? 1 : 0, in, const_cast<float*>(in), work, 3, s,
+                    hook, v_bf16, eps, in_split, KS_OUT_UPD_BF16);
 }
 
 bool ks_path(const KPlan& kp, int mode, int ncomp, long long cap) {

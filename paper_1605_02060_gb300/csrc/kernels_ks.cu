@@ -117,6 +117,12 @@ __device__ __forceinline__ void add_bf8(uint4 w, float* x) {
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
+// The 16-byte-aligned part of [p, p + bytes) into L2 (nothing when it is empty).
+__device__ __forceinline__ void prefetch_l2_inner(const void* p, uint32_t bytes) {
+  const uintptr_t a = ((uintptr_t)p + 15u) & ~(uintptr_t)15u;
+  const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15u;
+  if (e > a) prefetch_l2(reinterpret_cast<const void*>(a), (uint32_t)(e - a));
+}
 
 // Element offset of (line l, column 0): l = (a D + b) E + e -> (a F + b) P + e.
 __device__ __forceinline__ long long out_base(const KsOut& o, long long l) {
@@ -142,6 +148,16 @@ __device__ __forceinline__ void store_scalar(const KsOut& o, int split, float ep
         if (split) oh[o.plane + off] = lo;
       }
     }
+  } else if (o.kind == KS_OUT_UPD_BF16) {
+    __nv_bfloat16* ob = reinterpret_cast<__nv_bfloat16*>(o.out);
+#pragma unroll
+    for (int j = 0; j < NMAX; ++j) {
+      if (j < cnt) {
+        const long long off = base + (long long)(n0 + j) * o.G;
+        const float w = __bfloat162float(ob[off]);
+        ob[off] = __float2bfloat16_rn(w - eps * (2.f * w - vc[j]));
+      }
+    }
   } else {
     float* of = reinterpret_cast<float*>(o.out);
 #pragma unroll
@@ -159,6 +175,18 @@ __device__ __forceinline__ void store_scalar(const KsOut& o, int split, float ep
   }
 }
 
+__device__ __forceinline__ bool is_upd(int kind) { return kind == KS_OUT_UPD || kind == KS_OUT_UPD_BF16; }
+
+// 4 consecutive bf16 (8 bytes) <-> float4
+__device__ __forceinline__ float4 bf4_to_f4(uint2 u) {
+  return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                     __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+}
+__device__ __forceinline__ uint2 f4_to_bf4(float4 w) {
+  const __nv_bfloat162 a = __floats2bfloat162_rn(w.x, w.y), b = __floats2bfloat162_rn(w.z, w.w);
+  return make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(uint16_t a, uint16_t b) {
   return (uint32_t)a | ((uint32_t)b << 16);
 }
@@ -174,12 +202,17 @@ __device__ __forceinline__ uint32_t pack_bf16x2(uint16_t a, uint16_t b) {
 __device__ __forceinline__ void load_old_rows(const KsOut& o, int lane, long long line0,
                                               long long nlines, int n0, int ncols, float4* old) {
   const float* of = reinterpret_cast<const float*>(o.out);
+  const uint16_t* ob = reinterpret_cast<const uint16_t*>(o.out);
 #pragma unroll
   for (int it = 0; it < 4; ++it) {
     const int idx = it * 32 + lane, r = idx >> 2, c4 = (idx & 3) * 4;
     const long long l = line0 + r;
-    if (l < nlines && n0 + c4 + 4 <= ncols)
-      old[it] = *reinterpret_cast<const float4*>(of + l * o.P + n0 + c4);
+    if (l < nlines && n0 + c4 + 4 <= ncols) {
+      if (o.kind == KS_OUT_UPD_BF16)
+        old[it] = bf4_to_f4(*reinterpret_cast<const uint2*>(ob + l * o.P + n0 + c4));
+      else
+        old[it] = *reinterpret_cast<const float4*>(of + l * o.P + n0 + c4);
+    }
   }
 }
 
@@ -218,12 +251,16 @@ __device__ __forceinline__ void store_rows(const KsOut& o, int split, float eps,
       if (l < nlines && n0 + c4 + 4 <= ncols) {
         const float* q = sg + r * KS_SROW + c4;
         float4 w = make_float4(q[0], q[1], q[2], q[3]);
-        if (o.kind == KS_OUT_UPD) {
+        if (is_upd(o.kind)) {
           const float4 p = old[it];
           w = make_float4(p.x - eps * (2.f * p.x - w.x), p.y - eps * (2.f * p.y - w.y),
                           p.z - eps * (2.f * p.z - w.z), p.w - eps * (2.f * p.w - w.w));
         }
-        *reinterpret_cast<float4*>(of + l * o.P + n0 + c4) = w;
+        if (o.kind == KS_OUT_UPD_BF16)
+          *reinterpret_cast<uint2*>(reinterpret_cast<uint16_t*>(o.out) + l * o.P + n0 + c4) =
+              f4_to_bf4(w);
+        else
+          *reinterpret_cast<float4*>(of + l * o.P + n0 + c4) = w;
       }
     }
   }
@@ -384,9 +421,11 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
       bool ok = true;
       for (int i = 0; i < my_tiles && ok; ++i) {
         const long long lt = (long long)(blockIdx.x + i * gridDim.x) * 128 + m;
-        if (a.o.kind == KS_OUT_UPD && lt < a.nlines)      // the old v of the tail columns
-          prefetch_l2(reinterpret_cast<const float*>(a.o.out) + lt * a.o.P + 256,
-                      (uint32_t)a.tw * 4u);   // tw = 4 or 8: x lengths are multiples of 4
+        if (is_upd(a.o.kind) && lt < a.nlines) {    // the old v of the tail columns
+          const int es = a.o.kind == KS_OUT_UPD_BF16 ? 2 : 4;
+          prefetch_l2_inner(reinterpret_cast<const char*>(a.o.out) + (lt * a.o.P + 256) * es,
+                            (uint32_t)(a.tw * es));
+        }
         float acc[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[j] = 0.f;
@@ -451,14 +490,15 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
       const long long line0 = l - lane;
       // the update reads the old v of this warp's columns: start bringing it into L2 while the
       // tensor cores are still on the tile
-      if (o.kind == KS_OUT_UPD && valid && cend * 16 > cbeg * 16) {
+      if (is_upd(o.kind) && valid && cend * 16 > cbeg * 16) {
         const int c1 = min(cend * 16, Lc);
+        const int es = o.kind == KS_OUT_UPD_BF16 ? 2 : 4;
         if (c1 > cbeg * 16)
-          prefetch_l2(reinterpret_cast<const float*>(o.out) + l * o.P + cbeg * 16,
-                      (uint32_t)(c1 - cbeg * 16) * 4u);
+          prefetch_l2_inner(reinterpret_cast<const char*>(o.out) + (l * o.P + cbeg * 16) * es,
+                            (uint32_t)((c1 - cbeg * 16) * es));
       }
       float4 oldv[8];
-      if (o.kind == KS_OUT_UPD && cbeg < cend) {
+      if (is_upd(o.kind) && cbeg < cend) {
         load_old_rows(o, lane, line0, a.nlines, cbeg * 16, ncols, oldv);
         if (cbeg + 1 < cend) load_old_rows(o, lane, line0, a.nlines, cbeg * 16 + 16, ncols, oldv + 4);
       }
@@ -467,7 +507,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
       const uint32_t trow = tmem + (uint32_t)(ab * a.Nc) + ((uint32_t)(q * 32) << 16);
       for (int cp = cbeg; cp < cend; cp += 2) {
         const int npair = min(2, cend - cp);
-        if (o.kind == KS_OUT_UPD && cp > cbeg) {
+        if (is_upd(o.kind) && cp > cbeg) {
           // the old v of this pair of chunks (the first pair was requested before the wait)
           load_old_rows(o, lane, line0, a.nlines, cp * 16, ncols, oldv);
           if (npair == 2) load_old_rows(o, lane, line0, a.nlines, cp * 16 + 16, ncols, oldv + 4);

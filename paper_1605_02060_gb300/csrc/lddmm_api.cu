@@ -370,11 +370,14 @@ int run_step(lddmm_ctx* ctx) {
     launch_fwd_flow(g, vj, uc, unx, dtx, dty, dtz, j == T - 1, L.I0, L.I1, L.M, ctx->J0T,
                     ctx->acc, s, ctx->st, rk_of(ctx));
     hk(KID_FWD_FLOW, 1);
-    // K b_j and the update v_j <- v_j - eps (2 v_j - K b_j): fused into the last DFT pass for
-    // float storage, a separate pass for bf16 storage
+    // K b_j and the update v_j <- v_j - eps (2 v_j - K b_j): fused into the last DFT pass (for
+    // bf16 storage on the pre-split path too), else a separate pass
     if (ctx->st == 0) {
       CK(apply_K(L.kp, ctx->p.k_mode, ctx->b, ctx->b, ctx->work, 3, s, hk, (float*)vj, ctx->eps,
                  ctx->kcap, ks));
+    } else if (ks) {
+      CK(apply_K_update_bf16(L.kp, ctx->p.k_mode, ctx->b, ctx->work, s, hk, vj, ctx->eps,
+                             ctx->kcap, ks));
     } else {
       CK(apply_K(L.kp, ctx->p.k_mode, ctx->b, ctx->b, ctx->work, 3, s, hk, nullptr, 0.f,
                  ctx->kcap, ks));
