@@ -489,65 +489,18 @@ def measure_extras(L, I0, I1, M, stream, dev):
 
 
 def measure_warm_start():
-    """Time to the plain method's energy with and without the learned warm start, at 32^3:
-    a 4-level encoder-decoder (16/32/64/128 channels) trained on the GPU by the library's own
-    kernels on 240 ellipsoid-union pairs (x8 mirror images) labelled by 60 plain iterations;
-    on 8 held-out pairs the warm start (prediction smoothed by gamma^2 K, scaled by the energy)
-    iterates until it reaches the energy of 60 plain iterations.  Both use backtracking (a step
-    that raises the energy is undone, the step size halved): with a fixed step the plain energy
-    is not monotone.  Wall times include context creation, prediction, the start's energy
-    evaluations and undone steps."""
-    import numpy as np
-
-    from paper_1605_02060_gb300 import surrogate as SG
-    n, T, iters = 32, 10, 60
-    t0 = time.perf_counter()
-    X, Y = SG.label_pairs(SG.make_pairs(240, n, seed0=1000, amp_max=4.0), iters, T)
-    X, Y = SG.augment_flips(X, Y, T)
-    net = SG.UNet3D(n=n, batch=8, seed=0, out_scale=float(np.sqrt((Y ** 2).mean())))
-    SG.train(net, X, Y, epochs=6, lr=1e-3)
-    train_s = time.perf_counter() - t0
-    rows = []
-    for pr in SG.make_pairs(8, n, seed0=5000, amp_max=4.0):
-        # both runs with backtracking, so that their energies never rise: the plain target is
-        # its energy after 60 accepted iterations
-        _, E, _, _ = SG.run_plain(pr, iters, T, flags=1)
-        it_p, wall_p, dice_p = SG.run_plain_timed(pr, E[-1], 2 * iters, T, flags=1)
-        it_w, c, _, wall_w = SG.run_warm(net, pr, E[-1], 2 * iters, T, flags=1)
-        e_w = SG.run_warm.last_start_energy
-        # the geodesic variant: only the prediction's v_0, with v_1..v_{T-1} shot from it
-        it_s, _, _, wall_s = SG.run_warm(net, pr, E[-1], 2 * iters, T, flags=1, shoot=True)
-        e_s = SG.run_warm.last_start_energy
-        # time to the plain method's Dice: the fewest warm iterations that match it (found
-        # untimed), then a timed run of exactly that many
-        kd = SG.warm_iters_to_dice(net, pr, dice_p, 2 * iters, T, flags=1)
-        wall_d = SG.run_warm_fixed(net, pr, kd, T, flags=1) if kd is not None else float("nan")
-        rows.append((it_p, wall_p, dice_p, it_w, wall_w, SG.run_warm.last_dice,
-                     SG.warm_start_dice(net, pr, T), -1 if kd is None else kd, wall_d,
-                     it_s, wall_s, e_w, e_s, E[0]))
-    a = np.array(rows, dtype=np.float64)
-    okd = a[:, 7] >= 0
-    return {"grid": "32^3", "T": T, "train_pairs": 240, "mirror_images": 8, "epochs": 6,
-            "held_out": len(rows), "plain_iters": iters, "train_s": round(train_s, 1),
-            "plain_iters_to_energy": a[:, 0].astype(int).tolist(),
-            "warm_iters_to_energy": a[:, 3].astype(int).tolist(),
-            "plain_wall_ms_mean": round(1e3 * a[:, 1].mean(), 1),
-            "warm_wall_ms_mean": round(1e3 * a[:, 4].mean(), 1),
-            "wall_speedup": round(a[:, 1].sum() / a[:, 4].sum(), 3),
-            "wall_speedup_per_pair": [round(float(x), 2) for x in a[:, 1] / a[:, 4]],
-            "wall_speedup_median": round(float(np.median(a[:, 1] / a[:, 4])), 2),
-            "warm_reached": int((a[:, 3] < 2 * iters).sum()),
-            "dice_plain": round(a[:, 2].mean(), 4), "dice_warm": round(a[:, 5].mean(), 4),
-            "dice_surrogate_only": round(a[:, 6].mean(), 4),
-            "warm_iters_to_plain_dice": a[:, 7].astype(int).tolist(),
-            "warm_to_dice_wall_ms_mean": round(1e3 * float(np.nanmean(a[okd, 8])), 1) if okd.any() else None,
-            "dice_wall_speedup": round(float(a[okd, 1].sum() / a[okd, 8].sum()), 3) if okd.all() else None,
-            "shot_iters_to_energy": a[:, 9].astype(int).tolist(),
-            "shot_wall_ms_mean": round(1e3 * a[:, 10].mean(), 1),
-            "shot_wall_speedup_median": round(float(np.median(a[:, 1] / a[:, 10])), 2),
-            "start_energy_rel_plain_start": {
-                "predicted_field": [round(float(x), 3) for x in a[:, 11] / a[:, 13]],
-                "shot_from_predicted_v0": [round(float(x), 3) for x in a[:, 12] / a[:, 13]]}}
+    """Time to the plain method's final masked-SSD energy and Dice at 264x160x228 with and without
+    the learned warm start (the 64^3 network shipped in the package, trained on 2000 converged
+    plain runs): plain LDDMM from v = 0 to convergence, then the warm start until its E_data and
+    Dice reach the plain ones, for the bf16x3 K, plain bf16 K and bf16-storage variants.  Wall
+    times include context creation, the network's prediction and the scale search."""
+    from paper_1605_02060_gb300 import warm64 as W
+    if not os.path.exists(W.WEIGHTS):
+        return {"unavailable": "no trained network at %s" % os.path.relpath(W.WEIGHTS, ROOT)}
+    net = W.load_net(W.WEIGHTS)
+    out = W.measure(net)
+    out["surrogate_only_dice"] = round(W.surrogate_only_dice(net), 5)
+    return out
 
 
 def ctypes_sizeof_energy():
@@ -582,7 +535,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-warm-start", action="store_true",
-                    help="skip the learned warm-start measurement (about a minute)")
+                    help="skip the learned warm-start measurement (a few seconds)")
     ap.add_argument("--grid", type=int, nargs=3, default=None, metavar=("X", "Y", "Z"),
                     help="override the 264 160 228 grid (tests only; the metric is quoted on the "
                          "default)")

@@ -10,13 +10,17 @@ most 500 iterations.
 At a registration of size (X, Y, Z) the masks are resampled to 64^3 (cell-centred trilinear),
 the predicted v_0 is resampled back with its components scaled to voxels of the registration
 grid (x by X/64, y by Y/64, z by Z/64; the network grid is an anisotropic resample of the box),
-smoothed by gamma^2 K, and v_1..v_{T-1} are shot from it along the geodesic (EPDiff, as
-lddmm_shoot).  Among c v_0 for a few scales c the one of lowest energy is kept (c = 0 is the
-plain start v = 0, so the warm start never starts above plain LDDMM); plain iterations follow.
+smoothed by gamma^2 K and copied to every time step.  Among c v_0 for a few scales c the one of
+lowest energy is kept (c = 0 is the plain start v = 0, so the warm start never starts above
+plain LDDMM); plain iterations follow.  (Shooting v_1..v_{T-1} from v_0 along the geodesic,
+EPDiff as lddmm_shoot, is available as an option: at 264x160x228 the shot field grows from step
+to step for the predicted v_0 and its energy is not finite, so the copy is the default.)
 Every step runs in liblddmm's kernels; PyTorch holds the device memory.
 
+The network trained by the first command below ships as weights/warm64.npz (bf16 weights).
+
     python -m paper_1605_02060_gb300.warm64 train --out weights.npz [--pairs 2000]
-    python -m paper_1605_02060_gb300.warm64 measure --weights weights.npz
+    python -m paper_1605_02060_gb300.warm64 measure [--weights weights.npz]
 """
 from __future__ import annotations
 
@@ -33,7 +37,8 @@ from . import synth
 
 NG = 64                     # network grid
 CHANS = (16, 32, 64, 128)
-SCALES = (0.0, 0.5, 1.0)
+SCALES = (0.0, 0.125, 0.25, 0.375, 0.5, 0.75, 1.0)
+WEIGHTS = __import__("os").path.join(__import__("os").path.dirname(__file__), "weights", "warm64.npz")
 
 
 def _dev(a):
@@ -124,11 +129,20 @@ def train(X, Y, epochs, lr=1e-3, batch=8, seed=0, log=None):
     return net, hist
 
 
+def _bf16_bits(a):
+    """float32 -> bf16 bit patterns (round to nearest even), as uint16."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return u.astype(np.uint16)
+
+
 def save(net, path, meta=None):
+    """Weights as the bf16 the products use (uint16 bit patterns; the optimiser's FP32 master copy
+    is not kept), biases float32."""
     st = net.state()
     np.savez(path, out_scale=st["out_scale"], chans=np.array(st["chans"]),
              meta=json.dumps(meta or {}),
-             **{"w%d" % i: w for i, w in enumerate(st["w"])},
+             **{"w%d" % i: _bf16_bits(w) for i, w in enumerate(st["w"])},
              **{"b%d" % i: b for i, b in enumerate(st["b"])})
 
 
@@ -138,7 +152,13 @@ def load_net(path, batch=1):
     net = SG.UNet3D(chans=chans, cin=2, cout=3, n=NG, batch=batch, seed=0,
                     out_scale=float(d["out_scale"]))
     n = len(net.shapes)
-    net.load_state({"w": [d["w%d" % i] for i in range(n)], "b": [d["b%d" % i] for i in range(n)],
+
+    def w(i):
+        a = d["w%d" % i]
+        if a.dtype == np.uint16:                 # bf16 bit patterns
+            a = (a.astype(np.uint32) << 16).view(np.float32)
+        return np.ascontiguousarray(a, np.float32)
+    net.load_state({"w": [w(i) for i in range(n)], "b": [d["b%d" % i] for i in range(n)],
                     "out_scale": float(d["out_scale"])})
     return net
 
@@ -159,9 +179,11 @@ def predict_v0(net, I0, I1, out_shape):
     return L.resample(v64, out_shape, ncomp=3, scale=(s * nx / NG, s * ny / NG, s * nz / NG))
 
 
-def warm_start(ctx, net, I0, I1, scales=SCALES):
-    """Set the context's v to the best of c x (geodesic from the smoothed predicted v_0).
-    Returns (chosen c, its energy, energies of all candidates)."""
+def warm_start(ctx, net, I0, I1, scales=SCALES, shoot=False):
+    """Set the context's v to the candidate of lowest energy among c x (the smoothed predicted
+    v_0 copied to every time step), c in scales (c = 0: the plain start v = 0).  shoot=True
+    shoots v_1..v_{T-1} from c v_0 instead (EPDiff); a shot whose energy is not finite is
+    dropped.  Returns (chosen c, its energy, energies of all candidates)."""
     T = ctx.params.T
     shape = tuple(I0.shape)
     v0 = predict_v0(net, I0, I1, shape)
@@ -169,31 +191,33 @@ def warm_start(ctx, net, I0, I1, scales=SCALES):
     for c in range(3):                       # gamma^2 K: unit gain at frequency zero
         ctx.apply_K(v0[c], v0[c])
     L.scale_(v0, g2)
-    zero = torch.zeros((T, 3) + shape, device="cuda")
-    cand = torch.empty_like(v0)
+    cand = torch.empty((T, 3) + shape, device="cuda")
+
+    def put(c):
+        if c == 0.0:
+            cand.zero_()
+            ctx.set_velocity(cand)
+        elif shoot:
+            one = v0.clone()
+            L.scale_(one, c)
+            ctx.shoot(one)
+        else:
+            cand.copy_(v0.unsqueeze(0).expand(T, -1, -1, -1, -1))
+            L.scale_(cand, c)
+            ctx.set_velocity(cand)
+
     res = []
     for c in scales:
-        if c == 0.0:
-            ctx.set_velocity(zero)
-        else:
-            cand.copy_(v0)
-            L.scale_(cand, c)
-            ctx.shoot(cand)
+        put(c)
         try:
             res.append(ctx.energy()["total"])
-        except L.LddmmError as e:          # a shot that diverged is not a candidate
+        except L.LddmmError as e:          # a start whose energy is not finite is dropped
             if e.code != L.LDDMM_ERR_NONFINITE:
                 raise
             res.append(float("inf"))
     best = int(np.argmin(res))
-    c = scales[best]
-    if c == 0.0:
-        ctx.set_velocity(zero)
-    else:
-        cand.copy_(v0)
-        L.scale_(cand, c)
-        ctx.shoot(cand)
-    return c, res[best], res
+    put(scales[best])
+    return scales[best], res[best], res
 
 
 def run_warm(net, I0, I1, M, target_data, T=10, k_mode=1, storage=0, cap=500, dice_labels=None,
@@ -237,42 +261,60 @@ def run_warm(net, I0, I1, M, target_data, T=10, k_mode=1, storage=0, cap=500, di
             "reached": min(D) <= target_data and (dice_target is None or (dice or 0) >= dice_target)}
 
 
-def measure(net, T=10, k_mode=1, warm_k_mode=None, storage=0, log=None):
+WARM_VARIANTS = ((1, 0), (2, 0), (1, 1))     # (k_mode, storage) of the warm runs
+
+
+def measure(net, T=10, k_mode=1, variants=WARM_VARIANTS, log=None):
     """Time to the plain method's final masked-SSD energy and Dice at 264x160x228 (the brain
-    pair, seed 1).  Plain LDDMM runs from v = 0 to convergence (the labels' stop rule); its final
-    E_data = sigma^-2 h^3 sum M (I0 o phi_10 - I1)^2 and the Dice D of the transferred template
-    mask are the targets.  The warm start then iterates until E_data <= the plain value and
-    Dice >= D - 0.005.  Both wall times start at context creation.  warm_k_mode: the DFT
-    products of the warm run (default: as plain)."""
+    pair, seed 1).  Plain LDDMM (bf16x3 K unless k_mode says otherwise, float storage) runs from
+    v = 0 to convergence (the labels' stop rule); its final E_data = sigma^-2 h^3 sum M
+    (I0 o phi_10 - I1)^2 and the Dice D of the transferred template mask are the targets.  Each
+    warm variant (k_mode, storage) then iterates from the warm start until E_data <= the plain
+    value and Dice >= D - 0.005.  Both wall times start at context creation and include the
+    network's prediction, the resampling, the smoothing and the scale search."""
     pair, _ = synth.brain_pair(shape=(228, 160, 264), base_shape=(114, 80, 132), seed=1)
     I0, I1, M = _dev(pair.I0), _dev(pair.I1), _dev(pair.M)
     lab = ((pair.I0 > 0.5).astype(np.uint16), (pair.I1 > 0.5).astype(np.uint16))
-    plain = converged_plain(I0, I1, M, T=T, k_mode=k_mode, storage=storage, cap=2000,
-                            dice_labels=lab, timed=True)
+    plain = converged_plain(I0, I1, M, T=T, k_mode=k_mode, cap=2000, dice_labels=lab, timed=True)
     if log:
         log("plain: %d iterations, %.2f s, E %.4g (data %.4g), Dice %.4f" %
             (plain["iterations"], plain["wall_s"], plain["final_energy"], plain["final_data"],
              plain["dice"]))
-    wk = k_mode if warm_k_mode is None else warm_k_mode
-    warm = run_warm(net, I0, I1, M, plain["final_data"], T=T, k_mode=wk, storage=storage,
-                    cap=plain["iterations"], dice_labels=lab, dice_target=plain["dice"] - 0.005)
-    if log:
-        log("warm: scale %.2f, start E %.4g (plain start %.4g), %d iterations, %.3f s (start "
-            "%.3f s), E_data %.4g, Dice %.4f, reached %s" %
-            (warm["scale"], warm["start_energy"], plain["energies"][0], warm["iterations"],
-             warm["wall_s"], warm["start_s"], warm["data"][-1], warm["dice"], warm["reached"]))
-    return {"grid": "264x160x228", "T": T, "k_mode": k_mode, "warm_k_mode": wk,
-            "storage": storage,
-            "plain_iterations": plain["iterations"], "plain_wall_s": round(plain["wall_s"], 3),
-            "plain_final_energy": plain["final_energy"], "plain_final_data": plain["final_data"],
-            "plain_start_energy": plain["energies"][0], "plain_dice": round(plain["dice"], 5),
-            "warm_scale": warm["scale"], "warm_start_energy": warm["start_energy"],
-            "warm_candidates": warm["candidates"],
-            "warm_iterations": warm["iterations"], "warm_wall_s": round(warm["wall_s"], 3),
-            "warm_start_s": round(warm["start_s"], 3), "warm_final_data": warm["data"][-1],
-            "warm_final_energy": warm["energies"][-1], "warm_dice": round(warm["dice"], 5),
-            "warm_reached": bool(warm["reached"]),
-            "speedup": round(plain["wall_s"] / warm["wall_s"], 2)}
+    out = {"grid": "264x160x228", "T": T, "plain_k_mode": k_mode,
+           "plain_iterations": plain["iterations"], "plain_wall_s": round(plain["wall_s"], 3),
+           "plain_final_energy": plain["final_energy"], "plain_final_data": plain["final_data"],
+           "plain_start_energy": plain["energies"][0], "plain_dice": round(plain["dice"], 5),
+           "warm": []}
+    for wk, wst in variants:
+        warm = run_warm(net, I0, I1, M, plain["final_data"], T=T, k_mode=wk, storage=wst,
+                        cap=plain["iterations"], dice_labels=lab, dice_target=plain["dice"] - 0.005)
+        if log:
+            log("warm k_mode %d storage %d: scale %.3f, start E %.4g, %d iterations, %.3f s "
+                "(start %.3f s), E %.4g, E_data %.4g, Dice %.4f, reached %s" %
+                (wk, wst, warm["scale"], warm["start_energy"], warm["iterations"],
+                 warm["wall_s"], warm["start_s"], warm["energies"][-1], warm["data"][-1],
+                 warm["dice"], warm["reached"]))
+        out["warm"].append({
+            "k_mode": wk, "storage": wst, "scale": warm["scale"],
+            "start_energy": warm["start_energy"], "candidates": warm["candidates"],
+            "iterations": warm["iterations"], "wall_s": round(warm["wall_s"], 3),
+            "start_s": round(warm["start_s"], 3), "final_data": warm["data"][-1],
+            "final_energy": warm["energies"][-1], "dice": round(warm["dice"], 5),
+            "reached": bool(warm["reached"]),
+            "speedup": round(plain["wall_s"] / warm["wall_s"], 2)})
+    return out
+
+
+def measure_shot_start(net, T=10, k_mode=1):
+    """Energies of the shot starts (v_1..v_{T-1} by EPDiff from c v_0) at 264x160x228, for the
+    record: at this grid the shot field grows from step to step and its energy is not finite
+    for most scales."""
+    pair, _ = synth.brain_pair(shape=(228, 160, 264), base_shape=(114, 80, 132), seed=1)
+    I0, I1, M = _dev(pair.I0), _dev(pair.I1), _dev(pair.M)
+    p = L.default_params(264, 160, 228, T=T, k_mode=k_mode, flags=1)
+    with L.Lddmm(p, I0, I1, M) as ctx:
+        c, e, cands = warm_start(ctx, net, I0, I1, scales=(0.0, 0.1, 0.25, 0.5, 1.0), shoot=True)
+    return {"shot_scales": [0.0, 0.1, 0.25, 0.5, 1.0], "shot_energies": cands, "chosen": c}
 
 
 def surrogate_only_dice(net, T=10, k_mode=1):
@@ -282,7 +324,7 @@ def surrogate_only_dice(net, T=10, k_mode=1):
     I0, I1, M = _dev(pair.I0), _dev(pair.I1), _dev(pair.M)
     p = L.default_params(264, 160, 228, T=T, k_mode=k_mode, flags=1)
     with L.Lddmm(p, I0, I1, M) as ctx:
-        warm_start(ctx, net, I0, I1, scales=(1.0,))
+        warm_start(ctx, net, I0, I1, scales=SCALES[1:])
         return ctx.dice(ctx.transfer_labels((pair.I0 > 0.5).astype(np.uint16)),
                         (pair.I1 > 0.5).astype(np.uint16))
 
@@ -291,7 +333,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("cmd", choices=["train", "measure"])
     ap.add_argument("--out", default="warm64.npz")
-    ap.add_argument("--weights", default="warm64.npz")
+    ap.add_argument("--weights", default=WEIGHTS)
     ap.add_argument("--pairs", type=int, default=2000)
     ap.add_argument("--val", type=int, default=100)
     ap.add_argument("--epochs", type=int, default=20)
@@ -321,7 +363,7 @@ def main():
         res = measure(net, log=log)
         res["surrogate_only_dice"] = surrogate_only_dice(net)
         log(json.dumps(res))
-        log(json.dumps(measure(net, warm_k_mode=2, log=log)))
+        log(json.dumps(measure_shot_start(net)))
 
 
 if __name__ == "__main__":
