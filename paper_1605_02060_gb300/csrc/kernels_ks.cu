@@ -18,9 +18,13 @@
 //   warps 2-9   epilogue: tcgen05.ld of 16/32 columns (warp w reads TMEM lanes 32(w%4)..+31, the
 //               two warps of a lane quadrant split the columns), optional K symbol or the
 //               gradient-descent update, stores;
-//   warps 10-13 x axis longer than 256 only: the output columns 256.. in FP32 on the CUDA cores,
+//   warps 10-13 x axis longer than 256: the output columns 256.. in FP32 on the CUDA cores,
 //               one line per thread, read from the same A stages (hi + lo) as the MMA; an A
 //               stage is free once the MMA has committed and these 128 threads have arrived.
+//               Passes without such columns whose outputs are transposed give these warps to
+//               the epilogue (three warps per TMEM lane quadrant instead of two): the epilogue's
+//               element-wise conversions and stores, not the tensor cores, set those passes'
+//               pace, and more warps hide more of their latency.
 // Every wait is bounded and observes a CTA-wide abort flag; on abort the kernel drains its
 // copies and MMAs, frees TMEM and reports through *err.
 #include <cuda.h>
@@ -40,7 +44,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 constexpr int KS_NT = 448;
 constexpr int KS_W_TMA = 0, KS_W_MMA = 1, KS_W_TAIL = 10;
-constexpr int KS_NEPI = 8;                 // epilogue warps 2..9
+constexpr int KS_NEPI = 8;                 // epilogue warps 2..9 (the transposed outputs of the
+                                           // passes without FP32 tail columns: 2..13)
 constexpr int KS_NTAIL = 128;              // tail threads (warps 10..13)
 constexpr int KS_ABOX = 128 * 128;         // one A box: 128 lines x 64 bf16 (16 KB)
 constexpr int KS_MAXS = 6;                 // ring depths (A and streamed B) at most
@@ -71,8 +76,19 @@ __host__ __device__ inline int ks_bbytes(int split, int Nc) { return (split ? 2 
 __host__ __device__ inline int ks_tbytes(const KsArgs& a) { return a.tw ? a.nkb * 64 * 8 * 4 : 0; }
 // per epilogue warp: 32 lines x 16 columns of fp32, rows padded to 17 (conflict-free transpose)
 constexpr int KS_SROW = 17;
+// transposed split outputs: per column range (2 or 3 of them), a tile of 16 columns x 128 lines
+// of bf16 hi and lo, through which the four lane-quadrant warps of the range store runs of 128
+// consecutive lines
+constexpr int KS_CTILE = 2 * 16 * 128 * 2;
+// (only when the output rows hold a multiple of 8 lines, so that the 8-line pieces are aligned:
+// with other row lengths the per-lane stores measured faster)
+__host__ __device__ inline bool ks_staged(const KsArgs& a) {
+  return a.o.G != 1 && a.o.kind == KS_OUT_SPLIT && a.o.E % 8 == 0;
+}
+__host__ __device__ inline int ks_nparts(const KsArgs& a) { return (a.tw == 0 && ks_staged(a)) ? 3 : 2; }
 __host__ __device__ inline int ks_sbytes(const KsArgs& a) {
-  return a.o.G == 1 ? KS_NEPI * 32 * KS_SROW * 4 : 0;
+  if (a.o.G == 1) return KS_NEPI * 32 * KS_SROW * 4;   // row outputs: 8 epilogue warps
+  return ks_staged(a) ? ks_nparts(a) * KS_CTILE : 0;
 }
 __host__ __device__ inline int ks_smem(const KsArgs& a) {
   return 1024 + a.AS * ks_abytes(a.split) + (a.bres ? a.nkb : a.BS) * ks_bbytes(a.split, a.Nc) +
@@ -278,6 +294,10 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
   __shared__ int abort_sh;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // epilogue warps: 2..9, and 10..13 as well when they have no tail columns to compute and the
+  // outputs are transposed (row outputs stage through 8 per-warp shared-memory tiles)
+  const bool wide = ks_nparts(a) == 3;
+  const int nepi = wide ? 12 : KS_NEPI;
   uint8_t* smem = smem_dyn + ((1024u - (ptx::smem_u32(smem_dyn) & 1023u)) & 1023u);
   const int abytes = ks_abytes(a.split), bbytes = ks_bbytes(a.split, a.Nc);
   uint8_t* aring = smem;
@@ -301,7 +321,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
     }
     for (int i = 0; i < 2; ++i) {
       ptx::mbar_init(ptx::smem_u32(&b_tfull[i]), 1);
-      ptx::mbar_init(ptx::smem_u32(&b_tempty[i]), 32 * KS_NEPI);
+      ptx::mbar_init(ptx::smem_u32(&b_tempty[i]), 32 * nepi);
     }
     ptx::mbar_init(ptx::smem_u32(&b_fin), 1);
     ptx::fence_mbar_init();
@@ -408,7 +428,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
     m_done:
       ptx::mma_commit(ptx::smem_u32(&b_fin));
     }
-  } else if (warp >= KS_W_TAIL) {
+  } else if (warp >= KS_W_TAIL && !wide) {
     // ------------------------------------------------------------ FP32 tail columns
     if (a.tw) {
       const int m = threadIdx.x - KS_W_TAIL * 32;             // line of the tile
@@ -462,11 +482,11 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
       }
     }
   } else {
-    // ------------------------------------------------------------ epilogue (warps 2-9)
+    // ------------------------------------------------------------ epilogue (warps 2-9 or 2-13)
     const int q = warp & 3;                          // TMEM lane quadrant of this warp
-    const int half = warp >= 6 ? 1 : 0;
-    const int nch = a.Nc / 16, nh = (nch + 1) / 2;
-    const int cbeg = half ? nh : 0, cend = half ? nch : nh;
+    const int part = (warp - 2) >> 2, nparts = nepi >> 2;   // column range of this warp
+    const int nch = a.Nc / 16;
+    const int cbeg = part * nch / nparts, cend = (part + 1) * nch / nparts;
     const KsOut& o = a.o;
     const int Lc = min(a.L, a.Nc);                   // valid tensor-core output columns
     // columns written per line (row-wise split outputs stop at the row pitch)
@@ -502,9 +522,79 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
         load_old_rows(o, lane, line0, a.nlines, cbeg * 16, ncols, oldv);
         if (cbeg + 1 < cend) load_old_rows(o, lane, line0, a.nlines, cbeg * 16 + 16, ncols, oldv + 4);
       }
-      if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tfull[ab]), use & 1, abort, a.poll)) break;
+      const bool staged = ks_staged(a);
+      int got = ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tfull[ab]), use & 1, abort, a.poll) ? 1 : 0;
+      if (staged) {
+        // the four warps of a column range meet at named barriers below: they give up together
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.s32 p, %1, 0;\n\t"
+            "bar.red.and.pred p, %2, 128, p;\n\tselp.s32 %0, 1, 0, p;\n\t}"
+            : "=r"(got)
+            : "r"(got), "r"(2 + part)
+            : "memory");
+      }
+      if (!got) break;
       ptx::tc_fence_after();
       const uint32_t trow = tmem + (uint32_t)(ab * a.Nc) + ((uint32_t)(q * 32) << 16);
+      if (staged) {
+        // Transposed split output.  Per 16-column chunk the four quadrant warps of this column
+        // range write their lines' hi/lo bf16 into the range's shared tile [plane][col][line];
+        // then each of the 128 threads stores 16-byte pieces of 8 consecutive lines of one
+        // column, so that a warp instruction writes two runs of 128 lines (256 bytes) instead
+        // of 32 runs of one line.  A thread's line group g = its index % 16 is the same for
+        // every piece it stores, so its output offset is found once per tile.
+        uint16_t* tile = reinterpret_cast<uint16_t*>(stg) + part * (KS_CTILE / 2);
+        const int tp = q * 32 + lane, grp = tp & 15;
+        const long long lg0 = line0 - q * 32 + grp * 8;     // first line of this thread's group
+        const long long gb = lg0 < a.nlines ? out_base(o, lg0) : 0;
+        // 8 lines in one run: one 16-byte store when 16-byte aligned, else two of 8 bytes.  A
+        // group that crosses the end of an output row (E lines) continues at the next row's
+        // base nb from its line k on.
+        const bool run = lg0 + 7 < a.nlines && out_base(o, lg0 + 7) == gb + 7;
+        const int vec = !run ? 0 : ((gb & 7) == 0 ? 2 : ((gb & 3) == 0 ? 1 : 0));
+        const int kcut = run ? 8 : (int)min((long long)8, o.E - lg0 % o.E);
+        const long long nb = (!run && lg0 + kcut < a.nlines) ? out_base(o, lg0 + kcut) : 0;
+        const int np = a.split ? 2 : 1;
+        for (int c = cbeg; c < cend; ++c) {
+          float vc[16];
+          ptx::tmem_ld16(trow + (uint32_t)(c * 16), vc);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            uint16_t h, lo;
+            split1(vc[j], h, lo);
+            tile[j * 128 + tp] = h;
+            tile[(16 + j) * 128 + tp] = lo;
+          }
+          asm volatile("bar.sync %0, 128;" ::"r"(2 + part) : "memory");
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int k = tp + 128 * r, pl = k >> 8, j = (k >> 4) & 15, n = c * 16 + j;
+            if (pl < np && n < Lc) {
+              uint16_t* oh = reinterpret_cast<uint16_t*>(o.out) + (pl ? o.plane : 0);
+              const uint16_t* src = tile + (pl * 16 + j) * 128 + grp * 8;
+              if (vec == 2) {
+                *reinterpret_cast<uint4*>(oh + gb + (long long)n * o.G) =
+                    *reinterpret_cast<const uint4*>(src);
+              } else if (vec == 1) {
+                const uint4 w = *reinterpret_cast<const uint4*>(src);
+                uint2* d = reinterpret_cast<uint2*>(oh + gb + (long long)n * o.G);
+                d[0] = make_uint2(w.x, w.y);
+                d[1] = make_uint2(w.z, w.w);
+              } else {
+                for (int e = 0; e < 8; ++e) {
+                  if (lg0 + e < a.nlines) {
+                    // rows shorter than 8 lines: a group can span several of them
+                    const long long off = o.E < 8 ? out_base(o, lg0 + e)
+                                                  : (e < kcut ? gb + e : nb + (e - kcut));
+                    oh[off + (long long)n * o.G] = src[e];
+                  }
+                }
+              }
+            }
+          }
+          asm volatile("bar.sync %0, 128;" ::"r"(2 + part) : "memory");
+        }
+      } else
       for (int cp = cbeg; cp < cend; cp += 2) {
         const int npair = min(2, cend - cp);
         if (is_upd(o.kind) && cp > cbeg) {
