@@ -191,7 +191,10 @@ __device__ __forceinline__ void store_scalar(const KsOut& o, int split, float ep
   }
 }
 
-__device__ __forceinline__ bool is_upd(int kind) { return kind == KS_OUT_UPD || kind == KS_OUT_UPD_BF16; }
+__host__ __device__ inline bool is_upd_host(int kind) {
+  return kind == KS_OUT_UPD || kind == KS_OUT_UPD_BF16;
+}
+__device__ __forceinline__ bool is_upd(int kind) { return is_upd_host(kind); }
 
 // 4 consecutive bf16 (8 bytes) <-> float4
 __device__ __forceinline__ float4 bf4_to_f4(uint2 u) {
@@ -283,6 +286,18 @@ __device__ __forceinline__ void store_rows(const KsOut& o, int split, float eps,
   __syncwarp();
 }
 
+// Epilogue kinds: each pass is compiled with only its own output path, so that the registers of
+// the other paths do not count against it (the kernel runs at the 128-register limit of 448
+// threads).
+enum { EPI_T_STAGED = 0, EPI_T = 1, EPI_ROWS = 2, EPI_UPD = 3 };
+
+__host__ __device__ inline int ks_epi(const KsArgs& a) {
+  if (is_upd_host(a.o.kind)) return EPI_UPD;
+  if (a.o.G == 1) return EPI_ROWS;
+  return ks_staged(a) ? EPI_T_STAGED : EPI_T;
+}
+
+template <int EPI>
 __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUtensorMap tmA,
                                                      const __grid_constant__ CUtensorMap tmB,
                                                      KsArgs a) {
@@ -510,21 +525,23 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
       const long long line0 = l - lane;
       // the update reads the old v of this warp's columns: start bringing it into L2 while the
       // tensor cores are still on the tile
-      if (is_upd(o.kind) && valid && cend * 16 > cbeg * 16) {
+      if (EPI == EPI_UPD && valid && cend * 16 > cbeg * 16) {
         const int c1 = min(cend * 16, Lc);
         const int es = o.kind == KS_OUT_UPD_BF16 ? 2 : 4;
         if (c1 > cbeg * 16)
           prefetch_l2_inner(reinterpret_cast<const char*>(o.out) + (l * o.P + cbeg * 16) * es,
                             (uint32_t)((c1 - cbeg * 16) * es));
       }
+      // the update: the old v of the first pair of chunks is requested before the wait for the
+      // accumulator, each later pair's just before its TMEM load
       float4 oldv[8];
-      if (is_upd(o.kind) && cbeg < cend) {
+      if (EPI == EPI_UPD && cbeg < cend) {
         load_old_rows(o, lane, line0, a.nlines, cbeg * 16, ncols, oldv);
         if (cbeg + 1 < cend) load_old_rows(o, lane, line0, a.nlines, cbeg * 16 + 16, ncols, oldv + 4);
       }
-      const bool staged = ks_staged(a);
+      constexpr bool staged = EPI == EPI_T_STAGED;
       int got = ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tfull[ab]), use & 1, abort, a.poll) ? 1 : 0;
-      if (staged) {
+      if constexpr (staged) {
         // the four warps of a column range meet at named barriers below: they give up together
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.s32 p, %1, 0;\n\t"
@@ -536,7 +553,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
       if (!got) break;
       ptx::tc_fence_after();
       const uint32_t trow = tmem + (uint32_t)(ab * a.Nc) + ((uint32_t)(q * 32) << 16);
-      if (staged) {
+      if constexpr (staged) {
         // Transposed split output.  Per 16-column chunk the four quadrant warps of this column
         // range write their lines' hi/lo bf16 into the range's shared tile [plane][col][line];
         // then each of the 128 threads stores 16-byte pieces of 8 consecutive lines of one
@@ -594,11 +611,10 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
           }
           asm volatile("bar.sync %0, 128;" ::"r"(2 + part) : "memory");
         }
-      } else
+      } else {
       for (int cp = cbeg; cp < cend; cp += 2) {
         const int npair = min(2, cend - cp);
-        if (is_upd(o.kind) && cp > cbeg) {
-          // the old v of this pair of chunks (the first pair was requested before the wait)
+        if (EPI == EPI_UPD && cp > cbeg) {
           load_old_rows(o, lane, line0, a.nlines, cp * 16, ncols, oldv);
           if (npair == 2) load_old_rows(o, lane, line0, a.nlines, cp * 16 + 16, ncols, oldv + 4);
         }
@@ -617,11 +633,12 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
               vc[j] = __fdividef(vc[j], den * den);
             }
           }
-          if (o.G == 1)   // whole warp
+          if constexpr (EPI == EPI_ROWS || EPI == EPI_UPD)   // whole warp
             store_rows(o, a.split, a.eps, sg, lane, line0, a.nlines, n0, ncols, vc, oldv + 4 * u2);
           else if (valid)
             store_scalar<16>(o, a.split, a.eps, base, n0, vc, min(16, Lc - n0));
         }
+      }
       }
       ptx::tc_fence_before();
       ptx::mbar_arrive(ptx::smem_u32(&b_tempty[ab]));
@@ -776,7 +793,12 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
     if (a.BS < 2) return cudaErrorNotSupported;
   }
   const int smem = ks_smem(a);
-  cudaError_t e = cudaFuncSetAttribute(k_dft_ks, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const int epi = ks_epi(a);
+  auto kern = epi == EPI_T_STAGED ? k_dft_ks<EPI_T_STAGED>
+            : epi == EPI_T        ? k_dft_ks<EPI_T>
+            : epi == EPI_ROWS     ? k_dft_ks<EPI_ROWS>
+                                  : k_dft_ks<EPI_UPD>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   if (!g_ks_sms) {
     int dev = 0;
@@ -785,7 +807,7 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
     if (g_ks_sms <= 0) g_ks_sms = 148;
   }
   const int grid = a.ntiles < g_ks_sms ? a.ntiles : g_ks_sms;
-  if (grid > 0) k_dft_ks<<<grid, KS_NT, smem, s>>>(tmA, tmB, a);
+  if (grid > 0) kern<<<grid, KS_NT, smem, s>>>(tmA, tmB, a);
   return cudaGetLastError();
 }
 
