@@ -240,12 +240,13 @@ def run_reference(args):
     return 0
 
 
-def workload_config(kmode, ws=1):
+def workload_config(kmode, ws=1, storage=0):
     Z, Y, X = SHAPE
     N = X * Y * Z
     kname = {0: "fp32", 1: "bf16x3", 2: "bf16"}[kmode]
+    fields = "fp32 fields" if storage == 0 else "bf16 velocity and images"
     return {"workload": "masked LDDMM %dx%dx%d T=10, brain-shaped atlas/target mask pair (seed 1), "
-                        "fp32 fields, K via %s DFT products" % (X, Y, Z, kname),
+                        "%s, K via %s DFT products" % (X, Y, Z, fields, kname),
             "grid": [X, Y, Z], "T": T, "alpha": 0.02, "gamma": 1.0, "sigma": 0.1,
             "epsilon": 1e-3, "k_mode": kname, "parallelism": "replicas" if ws > 1 else "single",
             "l2": "working set %.1f GB > L2 (no flush)" % ((2 * T * 3 + 2 * T + 20) * N * 4 / 1e9)}
@@ -267,7 +268,7 @@ def run_ours(args):
     I1 = torch.from_numpy(pair.I1).to(dev)
     M = torch.from_numpy(pair.M).to(dev)
     stream = torch.cuda.Stream(device=dev)
-    p = L.default_params(X, Y, Z, T=T, k_mode=args.kmode)
+    p = L.default_params(X, Y, Z, T=T, k_mode=args.kmode, storage=args.storage)
     ctx = L.Lddmm(p, I0, I1, M, stream=stream)
     # warm-up
     for _ in range(args.warmup):
@@ -335,7 +336,9 @@ def run_ours(args):
     name, (nl, tot_ms) = dom
     avg_s = tot_ms / nl / 1000.0
     alg = algorithmic(name, N, (X, Y, Z), args.kmode, T, peaks)
-    traffic = _traffic(name)
+    if args.storage:                 # the table's bytes are those of fp32 storage
+        alg = {"bound": "n/a"}
+    traffic = _traffic(name) if not args.storage else None
     if alg["bound"] == "hbm":
         achieved = alg["bytes"] / avg_s / 1e9
         peak = peaks["hbm_gbs"]
@@ -350,6 +353,9 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": traffic, "kernel": name,
                 "peak_source": src + " (bf16 sustained)",
                 "launch_time": LAUNCH_TIME}
+    elif alg["bound"] == "n/a":
+        roof = {"bound": "n/a", "kernel": name,
+                "note": "algorithmic bytes are tabulated for fp32 storage only"}
     else:
         sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12   # FP32 FMA lanes x 2 flop x clock
@@ -365,10 +371,10 @@ def run_ours(args):
         dt = oracle_iteration(threads)
         cpu = {"value": 1.0 / (dt * _sample_scale()), "unit": UNIT, "cores": threads,
                "kind": "oracle", "sample": _sample_text(threads) + "; %.1f s" % dt}
-    cfg = workload_config(args.kmode, ws)
+    cfg = workload_config(args.kmode, ws, args.storage)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == 0 else "bf16",
             "data": "synthetic", "config": cfg,
             "clocks": clk, "e2e": e2e, "gpu_launches": int(sum(v[0] for v in prof.values())),
             "profiled_ms_per_step": ms_prof / args.steps,
@@ -532,6 +538,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--kmode", type=int, default=None, help="0 fp32, 1 bf16x3, 2 bf16")
+    ap.add_argument("--storage", type=int, default=0, choices=[0, 1],
+                    help="storage of v and the images: 0 fp32 (the metric's), 1 bf16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     ap.add_argument("--no-warm-start", action="store_true",

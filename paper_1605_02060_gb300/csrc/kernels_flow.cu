@@ -459,7 +459,7 @@ void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u
 // stencil is ALU work (about 12 FP32 operations a voxel), so the vector width cuts the
 // per-voxel instruction count; a field is read once from DRAM.  Per-plane partial sums are
 // FP32, accumulated with compensated (Kahan) addition per thread; the block total goes to FP64.
-constexpr int kEregZ = 16;
+constexpr int kEregZ = 32;
 
 template <int VEC>
 __device__ __forceinline__ void ldvec(const float* p, float (&o)[VEC]) {
