@@ -147,11 +147,12 @@ __device__ __forceinline__ long long out_base(const KsOut& o, long long l) {
 }
 
 // Store cnt (<= NMAX) consecutive output columns n0.. of one line, one element at a time
-// (transposed outputs whose runs are not vector aligned, and the FP32 tail columns).  The loops
+// (transposed outputs whose runs are not vector aligned, and the FP32 tail columns), split into
+// bf16 hi/lo or plain fp32 (the update's tail columns are stored by the tail threads).  The loops
 // are unrolled over NMAX so that vc stays in registers.
 template <int NMAX>
-__device__ __forceinline__ void store_scalar(const KsOut& o, int split, float eps, long long base,
-                                             int n0, const float* vc, int cnt) {
+__device__ __forceinline__ void store_scalar(const KsOut& o, int split, long long base, int n0,
+                                             const float* vc, int cnt) {
   if (o.kind == KS_OUT_SPLIT) {
     uint16_t* oh = reinterpret_cast<uint16_t*>(o.out);
 #pragma unroll
@@ -164,30 +165,11 @@ __device__ __forceinline__ void store_scalar(const KsOut& o, int split, float ep
         if (split) oh[o.plane + off] = lo;
       }
     }
-  } else if (o.kind == KS_OUT_UPD_BF16) {
-    __nv_bfloat16* ob = reinterpret_cast<__nv_bfloat16*>(o.out);
-#pragma unroll
-    for (int j = 0; j < NMAX; ++j) {
-      if (j < cnt) {
-        const long long off = base + (long long)(n0 + j) * o.G;
-        const float w = __bfloat162float(ob[off]);
-        ob[off] = __float2bfloat16_rn(w - eps * (2.f * w - vc[j]));
-      }
-    }
   } else {
     float* of = reinterpret_cast<float*>(o.out);
 #pragma unroll
-    for (int j = 0; j < NMAX; ++j) {
-      if (j < cnt) {
-        const long long off = base + (long long)(n0 + j) * o.G;
-        if (o.kind == KS_OUT_UPD) {
-          const float w = of[off];
-          of[off] = w - eps * (2.f * w - vc[j]);
-        } else {
-          of[off] = vc[j];
-        }
-      }
-    }
+    for (int j = 0; j < NMAX; ++j)
+      if (j < cnt) of[base + (long long)(n0 + j) * o.G] = vc[j];
   }
 }
 
@@ -455,11 +437,21 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
       uint32_t g = 0;
       bool ok = true;
       for (int i = 0; i < my_tiles && ok; ++i) {
-        const long long lt = (long long)(blockIdx.x + i * gridDim.x) * 128 + m;
-        if (is_upd(a.o.kind) && lt < a.nlines) {    // the old v of the tail columns
-          const int es = a.o.kind == KS_OUT_UPD_BF16 ? 2 : 4;
-          prefetch_l2_inner(reinterpret_cast<const char*>(a.o.out) + (lt * a.o.P + 256) * es,
-                            (uint32_t)(a.tw * es));
+        const long long l = (long long)(blockIdx.x + i * gridDim.x) * 128 + m;
+        // the update: the old v of the tail columns (row l at l * P) is loaded into registers
+        // before the products, so its latency passes while the k-blocks are summed
+        float oldt[8];
+        if constexpr (EPI == EPI_UPD) {
+          const bool bf = a.o.kind == KS_OUT_UPD_BF16;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            oldt[j] = 0.f;
+            if (l < a.nlines && j < a.tw) {
+              const long long off = l * a.o.P + 256 + j;
+              oldt[j] = bf ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(a.o.out)[off])
+                           : reinterpret_cast<const float*>(a.o.out)[off];
+            }
+          }
         }
         float acc[8];
 #pragma unroll
@@ -492,8 +484,22 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
           ptx::mbar_arrive(ptx::smem_u32(&b_aempty[s]));
         }
         if (!ok) break;
-        const long long l = (long long)(blockIdx.x + i * gridDim.x) * 128 + m;
-        if (l < a.nlines) store_scalar<8>(a.o, a.split, a.eps, out_base(a.o, l), 256, acc, a.tw);
+        if (l < a.nlines) {
+          if constexpr (EPI == EPI_UPD) {
+            const bool bf = a.o.kind == KS_OUT_UPD_BF16;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              if (j < a.tw) {
+                const long long off = l * a.o.P + 256 + j;
+                const float r = oldt[j] - a.eps * (2.f * oldt[j] - acc[j]);
+                if (bf) reinterpret_cast<__nv_bfloat16*>(a.o.out)[off] = __float2bfloat16_rn(r);
+                else reinterpret_cast<float*>(a.o.out)[off] = r;
+              }
+            }
+          } else {
+            store_scalar<8>(a.o, a.split, out_base(a.o, l), 256, acc, a.tw);
+          }
+        }
       }
     }
   } else {
@@ -636,7 +642,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
           if constexpr (EPI == EPI_ROWS || EPI == EPI_UPD)   // whole warp
             store_rows(o, a.split, a.eps, sg, lane, line0, a.nlines, n0, ncols, vc, oldv + 4 * u2);
           else if (valid)
-            store_scalar<16>(o, a.split, a.eps, base, n0, vc, min(16, Lc - n0));
+            store_scalar<16>(o, a.split, base, n0, vc, min(16, Lc - n0));
         }
       }
       }
