@@ -54,6 +54,7 @@ struct lddmm_ctx {
   float* J0T = nullptr;     // [N]
   float* stage = nullptr;   // [3][N] staging for host inputs / outputs
   Acc* acc = nullptr;
+  Acc* acc_init = nullptr;  // the accumulators' start value (device copy, written at creation)
   Acc* acc_host = nullptr;  // pinned
   int* flag = nullptr;      // device int
   unsigned long long* hist = nullptr;  // 3 x 65536
@@ -81,6 +82,17 @@ struct lddmm_ctx {
   float* gB = nullptr;      // dE/du_j
   float* seg = nullptr;     // recomputed segment of maps (checkpoint mode)
   int uall_slots = 0, seg_slots = 0;
+  // One iteration's launches recorded as a CUDA graph and replayed while the level, the step
+  // size and the velocity buffer are those it was recorded with (the kernels' arguments are
+  // part of the graph); the maps it leaves are the recorded ones.
+  cudaGraphExec_t step_graph = nullptr;
+  cudaStream_t cap_stream = nullptr;   // the graph is recorded on this stream (any context stream,
+                                       // the legacy one included, can then launch it)
+  int g_cur = -1;
+  float g_eps = 0.f;
+  const void* g_v = nullptr;
+  const float* g_u10 = nullptr;
+  const float* g_u01 = nullptr;
 };
 
 namespace {
@@ -263,8 +275,11 @@ void release(lddmm_ctx* ctx) {
   void* ps2[] = {ctx->uall, ctx->gA, ctx->gB, ctx->seg};
   for (void* p : ps2)
     if (p) cudaFree(p);
+  if (ctx->step_graph) cudaGraphExecDestroy(ctx->step_graph);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   void* ps[] = {ctx->v, ctx->v_tmp, ctx->v_prev, ctx->uB[0], ctx->uB[1], ctx->uF[0], ctx->uF[1], ctx->J1,
-                ctx->W, ctx->b, ctx->work, ctx->J0T, ctx->stage, ctx->acc, ctx->flag, ctx->hist};
+                ctx->W, ctx->b, ctx->work, ctx->J0T, ctx->stage, ctx->acc, ctx->acc_init, ctx->flag,
+                ctx->hist};
   for (void* p : ps)
     if (p) cudaFree(p);
   if (ctx->acc_host) cudaFreeHost(ctx->acc_host);
@@ -281,10 +296,14 @@ inline void* vptr(const lddmm_ctx* ctx, int j, int64_t N) {
   return reinterpret_cast<char*>(ctx->v) + (size_t)j * 3 * N * ctx->es;
 }
 
-int reset_acc(lddmm_ctx* ctx) {
+Acc acc_start() {
   Acc a{};
   a.min_det_ord = 0x7f7fffff;  // +FLT_MAX in the ordered encoding
-  CK(cudaMemcpyAsync(ctx->acc, &a, sizeof(Acc), cudaMemcpyHostToDevice, ctx->stream));
+  return a;
+}
+
+int reset_acc(lddmm_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->acc, ctx->acc_init, sizeof(Acc), cudaMemcpyDeviceToDevice, ctx->stream));
   return LDDMM_OK;
 }
 
@@ -326,7 +345,7 @@ int read_energy(lddmm_ctx* ctx, lddmm_energy* out, bool with_det) {
 }
 
 // One iteration: backward sweep, forward sweep with K and the update per time step.
-int run_step(lddmm_ctx* ctx) {
+int record_step(lddmm_ctx* ctx) {
   const Level& L = ctx->levels[ctx->cur];
   const Grid& g = L.g;
   const int T = ctx->p.T;
@@ -391,6 +410,57 @@ int run_step(lddmm_ctx* ctx) {
   ctx->u10 = uc;
   CK(cudaGetLastError());
   // The maps and J0_T describe the velocity before the update.
+  ctx->maps_valid = false;
+  ctx->j0_valid = false;
+  return LDDMM_OK;
+}
+
+// LDDMM_STEP_GRAPH=0 in the environment launches every iteration's kernels one by one.
+bool step_graph_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("LDDMM_STEP_GRAPH");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
+// One iteration, replayed from the recorded graph when it still applies (per-kernel timing
+// records each launch instead).  The graph saves the launch gaps between the ~100 kernels.
+int run_step(lddmm_ctx* ctx) {
+  if (ctx->prof_on || !step_graph_enabled()) return record_step(ctx);
+  if (!ctx->step_graph || ctx->g_cur != ctx->cur || ctx->g_eps != ctx->eps || ctx->g_v != ctx->v) {
+    if (ctx->step_graph) {
+      cudaGraphExecDestroy(ctx->step_graph);
+      ctx->step_graph = nullptr;
+    }
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
+    cudaStream_t user = ctx->stream;
+    ctx->stream = ctx->cap_stream;
+    const int rc = record_step(ctx);
+    ctx->stream = user;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    CK(e);
+    const cudaError_t ei = cudaGraphInstantiate(&ctx->step_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      ctx->step_graph = nullptr;
+      CK(ei);
+    }
+    ctx->g_cur = ctx->cur;
+    ctx->g_eps = ctx->eps;
+    ctx->g_v = ctx->v;
+    ctx->g_u10 = ctx->u10;
+    ctx->g_u01 = ctx->u01;
+  }
+  CK(cudaGraphLaunch(ctx->step_graph, ctx->stream));
+  ctx->u10 = ctx->g_u10;
+  ctx->u01 = ctx->g_u01;
   ctx->maps_valid = false;
   ctx->j0_valid = false;
   return LDDMM_OK;
@@ -587,13 +657,22 @@ int lddmm_create(const lddmm_params* p, const float* I0, const float* I1, const 
        A(dalloc(&ctx->uF[0], 3 * N)) && A(dalloc(&ctx->uF[1], 3 * N)) &&
        A(dalloc(&ctx->J1, T * N)) && A(dalloc(&ctx->W, T * N)) && A(dalloc(&ctx->b, ctx->kcap)) &&
        A(dalloc(&ctx->work, ctx->kcap)) && A(dalloc(&ctx->J0T, N)) && A(dalloc(&ctx->stage, 3 * N)) &&
-       A(dalloc(&ctx->acc, 1)) && A(dalloc(&ctx->flag, 1)) && A(dalloc(&ctx->hist, 3 * 65536)) &&
+       A(dalloc(&ctx->acc, 1)) && A(dalloc(&ctx->acc_init, 1)) && A(dalloc(&ctx->flag, 1)) &&
+       A(dalloc(&ctx->hist, 3 * 65536)) &&
        A(cudaMallocHost((void**)&ctx->acc_host, sizeof(Acc)));
   if (ok && (p->flags & 1)) ok = A(dalloc(&ctx->v_prev, ve));
   g_fail_alloc_countdown = 0;
   if (!ok) return bail(LDDMM_ERR_OOM);
   if (cudaMemsetAsync(ctx->v, 0, (size_t)ve * sizeof(float), ctx->stream) != cudaSuccess) {
     ctx->err = "memset failed";
+    return bail(LDDMM_ERR_CUDA);
+  }
+  // the accumulators' start value, copied from pinned memory in stream order (the pinned block
+  // is next written by the first energy read, which the stream orders after this copy)
+  *ctx->acc_host = acc_start();
+  if (cudaMemcpyAsync(ctx->acc_init, ctx->acc_host, sizeof(Acc), cudaMemcpyHostToDevice,
+                      ctx->stream) != cudaSuccess) {
+    ctx->err = "copy of the accumulator start value failed";
     return bail(LDDMM_ERR_CUDA);
   }
   rc = load_images(ctx, I0, I1, M);
