@@ -312,7 +312,7 @@ static cudaError_t apply_K_fp32(const KPlan& kp, const float* in, float* out, fl
 
 // Tensor-core K over pre-split intermediate fields.  Every pass reads its input with the
 // transformed axis contiguous and writes its output in the next pass's line order:
-//   x fwd:  [c][z][y][x]  (split, x rows, pitch Px)  -> [c][x'][z][y]  (split, y rows, pitch Py)
+//   x fwd:  [c][z][y][x]  (split, x rows, pitch Px)  -> [c][x'][Pz][y] (split, y rows, pitch Py)
 //   y fwd:                                            -> [c][x'][y'][z] (split, z rows, pitch Pz)
 //   z fwd + symbol:                                   -> [c][x'][y'][z'] (split, same order)
 //   z inv:                                            -> [c][z][x'][y'] (split, y rows, pitch Py)
@@ -320,6 +320,11 @@ static cudaError_t apply_K_fp32(const KPlan& kp, const float* in, float* out, fl
 //   x inv:                                            -> fp32 [c][z][y][x], or the update of v
 // The buffers alternate between work and out (in may alias out).  A plain fp32 input is first
 // split into work; without the update the result then lands in work and is copied to out.
+// The x forward output holds Pz (z rounded up to 8) planes per x' so that the y forward pass
+// runs over Pz lines per output row: its 8-line output pieces then start 16-byte aligned (the
+// staged epilogue).  Lines z >= nz are never written by the x pass and read whatever the buffer
+// holds; the y pass stores their results into the pitch padding of the z rows, which no later
+// pass reads (rows of a product are independent).
 static cudaError_t apply_K_ks(const KPlan& kp, int split, const float* in, float* out,
                               float* work, int ncomp, cudaStream_t s, const Hook& hook,
                               void* v_upd, float eps, bool in_split, int upd_kind = KS_OUT_UPD) {
@@ -343,8 +348,8 @@ static cudaError_t apply_K_ks(const KPlan& kp, int split, const float* in, float
     KsOut o;
   };
   const Pass ps[5] = {
-      {KID_KX_FWD, 0, false, C * Z * Y, {KS_OUT_SPLIT, 0, bA, C * X * Z * Py, Z, Y, X * Z, Py, Z * Py}},
-      {KID_KY_FWD, 1, false, C * X * Z, {KS_OUT_SPLIT, 0, bB, C * X * Y * Pz, 1, Z, Y, Pz, Pz}},
+      {KID_KX_FWD, 0, false, C * Z * Y, {KS_OUT_SPLIT, 0, bA, C * X * Pz * Py, Z, Y, X * Pz, Py, Pz * Py}},
+      {KID_KY_FWD, 1, false, C * X * Pz, {KS_OUT_SPLIT, 0, bB, C * X * Y * Pz, 1, Pz, Y, Pz, Pz}},
       {KID_KZ_SYM, 2, false, C * X * Y, {KS_OUT_SPLIT, 1, bA, C * X * Y * Pz, 1, 1, 1, Pz, 1}},
       {KID_KZ_INV, 2, true, C * X * Y, {KS_OUT_SPLIT, 0, bB, C * Z * X * Py, X, Y, Z * X, Py, X * Py}},
       {KID_KY_INV, 1, true, C * Z * X, {KS_OUT_SPLIT, 0, bA, C * Z * Y * Px, 1, X, Y, Px, Px}}};

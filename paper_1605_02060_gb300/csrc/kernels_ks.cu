@@ -21,7 +21,7 @@
 //   warps 10-13 x axis longer than 256: the output columns 256.. in FP32 on the CUDA cores,
 //               one line per thread, read from the same A stages (hi + lo) as the MMA; an A
 //               stage is free once the MMA has committed and these 128 threads have arrived.
-//               Passes without such columns whose outputs are transposed give these warps to
+//               Passes without such columns whose outputs are staged give these warps to
 //               the epilogue (three warps per TMEM lane quadrant instead of two): the epilogue's
 //               element-wise conversions and stores, not the tensor cores, set those passes'
 //               pace, and more warps hide more of their latency.
@@ -44,7 +44,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 constexpr int KS_NT = 448;
 constexpr int KS_W_TMA = 0, KS_W_MMA = 1, KS_W_TAIL = 10;
-constexpr int KS_NEPI = 8;                 // epilogue warps 2..9 (the transposed outputs of the
+constexpr int KS_NEPI = 8;                 // epilogue warps 2..9 (the staged outputs of the
                                            // passes without FP32 tail columns: 2..13)
 constexpr int KS_NTAIL = 128;              // tail threads (warps 10..13)
 constexpr int KS_ABOX = 128 * 128;         // one A box: 128 lines x 64 bf16 (16 KB)
@@ -85,9 +85,13 @@ constexpr int KS_CTILE = 2 * 16 * 128 * 2;
 __host__ __device__ inline bool ks_staged(const KsArgs& a) {
   return a.o.G != 1 && a.o.kind == KS_OUT_SPLIT && a.o.E % 8 == 0;
 }
-__host__ __device__ inline int ks_nparts(const KsArgs& a) { return (a.tw == 0 && ks_staged(a)) ? 3 : 2; }
+// Passes without FP32 tail columns whose outputs are staged (row outputs, or transposed ones
+// with aligned pieces) run 12 epilogue warps, three per TMEM lane quadrant; the others 8.
+__host__ __device__ inline int ks_nparts(const KsArgs& a) {
+  return (a.tw == 0 && (ks_staged(a) || a.o.G == 1)) ? 3 : 2;
+}
 __host__ __device__ inline int ks_sbytes(const KsArgs& a) {
-  if (a.o.G == 1) return KS_NEPI * 32 * KS_SROW * 4;   // row outputs: 8 epilogue warps
+  if (a.o.G == 1) return 4 * ks_nparts(a) * 32 * KS_SROW * 4;   // row outputs: a tile per warp
   return ks_staged(a) ? ks_nparts(a) * KS_CTILE : 0;
 }
 __host__ __device__ inline int ks_smem(const KsArgs& a) {
@@ -292,7 +296,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // epilogue warps: 2..9, and 10..13 as well when they have no tail columns to compute and the
-  // outputs are transposed (row outputs stage through 8 per-warp shared-memory tiles)
+  // outputs are staged
   const bool wide = ks_nparts(a) == 3;
   const int nepi = wide ? 12 : KS_NEPI;
   uint8_t* smem = smem_dyn + ((1024u - (ptx::smem_u32(smem_dyn) & 1023u)) & 1023u);
@@ -716,7 +720,7 @@ long long ks_field_floats(int nx, int ny, int nz, int ncomp) {
   const long long px = ks_pitch(nx), py = ks_pitch(ny), pz = ks_pitch(nz);
   long long m = X * Y * Z;                      // fp32 rows
   if (Z * Y * px > m) m = Z * Y * px;           // split [c][z][y][x] (x rows)
-  if (X * Z * py > m) m = X * Z * py;           // [c][x'][z][y] and [c][z][x'][y']
+  if (X * pz * py > m) m = X * pz * py;         // [c][x'][Pz][y] and [c][z][x'][y']
   if (X * Y * pz > m) m = X * Y * pz;           // [c][x'][y'][z]
   return m * ncomp;                             // two bf16 planes = one float per value
 }
