@@ -66,12 +66,13 @@ def algorithmic(kernel, N, dims, kmode, T=10, peaks=None):
     if kernel == "ereg":             # all T velocity fields read once: 12 B per voxel and step
         return {"bound": "hbm", "bytes": 12 * T * N}
     L = {"K_x_fwd": X, "K_x_inv_update": X, "K_y_fwd": Y, "K_y_inv": Y, "K_z_symbol": Z,
-         "K_z_inv": Z}[kernel]
+         "K_z_inv": Z, "K_z_fused": Z}[kernel]
     # one DFT pass over 3 components: field in and out (24 B/voxel; the fused update also reads
     # and writes v: 36 B/voxel); the mathematical product is 2 L flops per output value, which
-    # the bf16x3 tensor-core form computes three times (hi*hi + hi*lo + lo*hi)
+    # the bf16x3 tensor-core form computes three times (hi*hi + hi*lo + lo*hi); the fused z pass
+    # (forward product, symbol, inverse product) moves a pass's bytes and computes two products
     nbytes = (36 if kernel == "K_x_inv_update" else 24) * N
-    flops = 2.0 * L * 3 * N
+    flops = 2.0 * L * 3 * N * (2 if kernel == "K_z_fused" else 1)
     if kmode == 0:
         return {"bound": "alu", "flops": flops, "bytes": nbytes}
     hw_flops = flops * (3 if kmode == 1 else 1)

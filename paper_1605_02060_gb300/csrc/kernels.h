@@ -28,7 +28,7 @@ struct Hook {
 
 enum KernelId {
   KID_BACK_DISP = 0, KID_BACK_TERMS, KID_FWD_TERMS, KID_FWD_FLOW, KID_KX_FWD, KID_KY_FWD,
-  KID_KZ_SYM, KID_KZ_INV, KID_KY_INV, KID_KX_INV, KID_UPDATE, KID_EREG, KID_COUNT
+  KID_KZ_SYM, KID_KZ_INV, KID_KY_INV, KID_KX_INV, KID_UPDATE, KID_EREG, KID_KZ_FUSED, KID_COUNT
 };
 
 // ---- flows (kernels_flow.cu) ----
@@ -182,7 +182,8 @@ int ks_pitch(int L);
 bool ks_supported(const KPlan& kp);
 long long ks_field_floats(int nx, int ny, int nz, int ncomp);
 cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, const void* in,
-                         long long nlines, const KsOut& o, float eps, cudaStream_t s);
+                         long long nlines, const KsOut& o, float eps, cudaStream_t s,
+                         bool zz = false);
 // True when apply_K(kp, mode, ..., ncomp, cap) takes the pre-split path; its input may then be
 // given already split (in_split): bf16 hi/lo planes [ncomp][nz][ny][ks_pitch(nx)].
 bool ks_path(const KPlan& kp, int mode, int ncomp, long long cap);

@@ -341,27 +341,33 @@ static cudaError_t apply_K_ks(const KPlan& kp, int split, const float* in, float
     bA = out;
     bB = work;
   }
-  struct Pass {
+  // z forward, symbol and z inverse run as one fused pass when the z inverse output rows (y
+  // lines) hold a multiple of 8 lines; its output then lands where the z inverse pass puts it
+  const bool zz = Y % 8 == 0;
+  struct Pass2 {
     int kid, axis;
-    bool inv;
+    bool inv, zz;
     long long nlines;
     KsOut o;
   };
-  const Pass ps[5] = {
-      {KID_KX_FWD, 0, false, C * Z * Y, {KS_OUT_SPLIT, 0, bA, C * X * Pz * Py, Z, Y, X * Pz, Py, Pz * Py}},
-      {KID_KY_FWD, 1, false, C * X * Pz, {KS_OUT_SPLIT, 0, bB, C * X * Y * Pz, 1, Pz, Y, Pz, Pz}},
-      {KID_KZ_SYM, 2, false, C * X * Y, {KS_OUT_SPLIT, 1, bA, C * X * Y * Pz, 1, 1, 1, Pz, 1}},
-      {KID_KZ_INV, 2, true, C * X * Y, {KS_OUT_SPLIT, 0, bB, C * Z * X * Py, X, Y, Z * X, Py, X * Py}},
-      {KID_KY_INV, 1, true, C * Z * X, {KS_OUT_SPLIT, 0, bA, C * Z * Y * Px, 1, X, Y, Px, Px}}};
+  const Pass2 ps[5] = {
+      {KID_KX_FWD, 0, false, false, C * Z * Y, {KS_OUT_SPLIT, 0, bA, C * X * Pz * Py, Z, Y, X * Pz, Py, Pz * Py}},
+      {KID_KY_FWD, 1, false, false, C * X * Pz, {KS_OUT_SPLIT, 0, bB, C * X * Y * Pz, 1, Pz, Y, Pz, Pz}},
+      {KID_KZ_SYM, 2, false, false, C * X * Y, {KS_OUT_SPLIT, 1, bA, C * X * Y * Pz, 1, 1, 1, Pz, 1}},
+      {zz ? KID_KZ_FUSED : KID_KZ_INV, 2, true, zz, C * X * Y,
+       {KS_OUT_SPLIT, 0, zz ? bA : bB, C * Z * X * Py, X, Y, Z * X, Py, X * Py}},
+      {KID_KY_INV, 1, true, false, C * Z * X, {KS_OUT_SPLIT, 0, zz ? bB : bA, C * Z * Y * Px, 1, X, Y, Px, Px}}};
   for (int p = 0; p < 5; ++p) {
+    if (zz && p == 2) continue;
     hook(ps[p].kid, 0);
-    e = ks_axis_pass(kp, ps[p].axis, ps[p].inv, split, src, ps[p].nlines, ps[p].o, 0.f, s);
+    e = ks_axis_pass(kp, ps[p].axis, ps[p].inv, split, src, ps[p].nlines, ps[p].o, 0.f, s,
+                     ps[p].zz);
     hook(ps[p].kid, 1);
     if (e != cudaSuccess) return e;
     src = ps[p].o.out;
   }
-  // x inverse: from bA into v_upd (update) or fp32 rows
-  void* dst = v_upd ? v_upd : (void*)bB;
+  // x inverse: from the last output into v_upd (update) or fp32 rows in the other buffer
+  void* dst = v_upd ? v_upd : (void*)(src == bA ? bB : bA);
   const KsOut o6{v_upd ? upd_kind : KS_OUT_F32, 0, dst, 0, 1, 1, 1, X, 1};
   hook(KID_KX_INV, 0);
   e = ks_axis_pass(kp, 0, true, split, src, C * Z * Y, o6, eps, s);

@@ -69,6 +69,7 @@ struct KsArgs {
   int X, Y;            // symbol: line l = (c X + x) Y + y
   int* err;
   uint32_t poll;       // probes per pipeline wait before the CTA aborts
+  int zz;              // the fused z pass: forward product, symbol, inverse product
 };
 
 __host__ __device__ inline int ks_abytes(int split) { return (split ? 2 : 1) * KS_ABOX; }
@@ -275,9 +276,10 @@ __device__ __forceinline__ void store_rows(const KsOut& o, int split, float eps,
 // Epilogue kinds: each pass is compiled with only its own output path, so that the registers of
 // the other paths do not count against it (the kernel runs at the 128-register limit of 448
 // threads).
-enum { EPI_T_STAGED = 0, EPI_T = 1, EPI_ROWS = 2, EPI_UPD = 3 };
+enum { EPI_T_STAGED = 0, EPI_T = 1, EPI_ROWS = 2, EPI_UPD = 3, EPI_ZZ = 4 };
 
 __host__ __device__ inline int ks_epi(const KsArgs& a) {
+  if (a.zz) return EPI_ZZ;
   if (is_upd_host(a.o.kind)) return EPI_UPD;
   if (a.o.G == 1) return EPI_ROWS;
   return ks_staged(a) ? EPI_T_STAGED : EPI_T;
@@ -286,11 +288,17 @@ __host__ __device__ inline int ks_epi(const KsArgs& a) {
 template <int EPI>
 __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUtensorMap tmA,
                                                      const __grid_constant__ CUtensorMap tmB,
+                                                     const __grid_constant__ CUtensorMap tmB2,
                                                      KsArgs a) {
+  constexpr bool ZZ = EPI == EPI_ZZ;
   extern __shared__ __align__(1024) uint8_t smem_dyn[];
   __shared__ __align__(8) uint64_t b_afull[KS_MAXS], b_aempty[KS_MAXS], b_bfull[KS_MAXS],
       b_bempty[KS_MAXS];
   __shared__ __align__(8) uint64_t b_tfull[2], b_tempty[2], b_fin;
+  // the fused z pass: b_tfull[0] / [1] = forward / inverse accumulator full, b_tempty[1] = the
+  // inverse accumulator drained, b_a2[kb] = 64-column block kb of the scaled spectrum (the second
+  // product's A operand, in TMEM over the forward accumulator) converted
+  __shared__ __align__(8) uint64_t b_a2[4];
   __shared__ uint32_t tmem_sh;
   __shared__ int abort_sh;
 
@@ -325,6 +333,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
       ptx::mbar_init(ptx::smem_u32(&b_tempty[i]), 32 * nepi);
     }
     ptx::mbar_init(ptx::smem_u32(&b_fin), 1);
+    for (int i = 0; i < 4; ++i) ptx::mbar_init(ptx::smem_u32(&b_a2[i]), 128);
     ptx::fence_mbar_init();
     abort_sh = 0;
   }
@@ -341,6 +350,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
     if (lane == 0) {
       ptx::prefetch_tmap(&tmA);
       ptx::prefetch_tmap(&tmB);
+      if (ZZ) ptx::prefetch_tmap(&tmB2);
       const int np = a.split ? 2 : 1;
       if (a.bres && my_tiles > 0) {
         const uint32_t fb = ptx::smem_u32(&b_bfull[0]);
@@ -372,6 +382,19 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
             ++gb;
           }
         }
+        // the fused z pass streams the inverse table after the forward one, block by block
+        if (ZZ) {
+          for (int kb = 0; kb < nkb; ++kb) {
+            const int sb = (int)(gb % BS);
+            if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bempty[sb]), ((gb / BS) & 1) ^ 1, abort, a.poll)) goto p_done;
+            const uint32_t fb = ptx::smem_u32(&b_bfull[sb]);
+            ptx::mbar_arrive_expect_tx(fb, (uint32_t)bbytes);
+            for (int pl = 0; pl < np; ++pl)
+              ptx::tma_load_3d(ptx::smem_u32(bring + sb * bbytes + pl * a.Nc * 128), &tmB2,
+                               kb * 64, 0, pl, fb);
+            ++gb;
+          }
+        }
       }
     p_done:
       // copies still in flight (only after an abort can any remain unconsumed)
@@ -390,6 +413,71 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
       const uint32_t a0 = ptx::smem_u32(aring), b0 = ptx::smem_u32(bring);
       const uint32_t blo = (uint32_t)a.Nc * 128u;               // B lo plane offset
       uint32_t g = 0;
+      if constexpr (ZZ) {
+        // forward product into columns 0.. (A from the ring, B the forward table), then, block by
+        // block as the epilogue converts it, the inverse product of the scaled spectrum (A in
+        // TMEM over the forward accumulator, B the inverse table) into columns 256..
+        uint32_t gb = 0;
+        const uint32_t d2 = tmem + 256u;
+        for (int i = 0; i < my_tiles; ++i) {
+          // the forward accumulator still holds the previous tile's spectrum until the previous
+          // inverse product has completed
+          if (i > 0 && !ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tfull[1]), (uint32_t)(i - 1) & 1u, abort, a.poll)) break;
+          ptx::tc_fence_after();
+          bool ok = true;
+          for (int kb = 0; kb < nkb; ++kb, ++g, ++gb) {
+            const int s = (int)(g % AS), sb = (int)(gb % BS);
+            if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_afull[s]), (g / AS) & 1, abort, a.poll) ||
+                !ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bfull[sb]), (gb / BS) & 1, abort, a.poll)) {
+              ok = false;
+              break;
+            }
+            ptx::tc_fence_after();
+            const uint32_t as = a0 + (uint32_t)(s * abytes), bs = b0 + (uint32_t)(sb * bbytes);
+            const int nst = min(4, a.nk - kb * 4);
+            for (int j = 0; j < nst; ++j) {
+              const uint64_t dAh = desc_sw128(as + 32u * j), dBh = desc_sw128(bs + 32u * j);
+              ptx::mma_bf16(tmem, dAh, dBh, id, (kb | j) ? 1u : 0u);
+              if (a.split) {
+                const uint64_t dAl = desc_sw128(as + (uint32_t)KS_ABOX + 32u * j);
+                const uint64_t dBl = desc_sw128(bs + blo + 32u * j);
+                ptx::mma_bf16(tmem, dAh, dBl, id, 1u);
+                ptx::mma_bf16(tmem, dAl, dBh, id, 1u);
+              }
+            }
+            ptx::mma_commit(ptx::smem_u32(&b_aempty[s]));
+            ptx::mma_commit(ptx::smem_u32(&b_bempty[sb]));
+          }
+          if (!ok) break;
+          ptx::mma_commit(ptx::smem_u32(&b_tfull[0]));
+          if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tempty[1]), ((uint32_t)i & 1u) ^ 1u, abort, a.poll)) break;
+          for (int kb = 0; kb < nkb; ++kb, ++gb) {
+            const int sb = (int)(gb % BS);
+            if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_a2[kb]), (uint32_t)i & 1u, abort, a.poll) ||
+                !ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bfull[sb]), (gb / BS) & 1, abort, a.poll)) {
+              ok = false;
+              break;
+            }
+            ptx::tc_fence_after();
+            const uint32_t bs = b0 + (uint32_t)(sb * bbytes);
+            const int nst = min(4, a.nk - kb * 4);
+            for (int j = 0; j < nst; ++j) {
+              const uint32_t ta = tmem + (uint32_t)(16 * (kb * 4 + j));   // hi at ta, lo at ta + 8
+              const uint64_t dBh = desc_sw128(bs + 32u * j);
+              ptx::mma_bf16_ta(d2, ta, dBh, id, (kb | j) ? 1u : 0u);
+              if (a.split) {
+                const uint64_t dBl = desc_sw128(bs + blo + 32u * j);
+                ptx::mma_bf16_ta(d2, ta, dBl, id, 1u);
+                ptx::mma_bf16_ta(d2, ta + 8u, dBh, id, 1u);
+              }
+            }
+            ptx::mma_commit(ptx::smem_u32(&b_bempty[sb]));
+          }
+          if (!ok) break;
+          ptx::mma_commit(ptx::smem_u32(&b_tfull[1]));
+        }
+        goto m_done;
+      }
       if (a.bres && my_tiles > 0 &&
           !ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bfull[0]), 0u, abort, a.poll)) goto m_done;
       for (int i = 0; i < my_tiles; ++i) {
@@ -518,18 +606,55 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
     const int ncols = (o.G == 1 && o.kind == KS_OUT_SPLIT) ? min(a.Nc, (int)o.P) : Lc;
     float* sg = stg + (warp - 2) * (32 * KS_SROW);
     for (int i = 0; i < my_tiles; ++i) {
-      const int ab = i & 1;
-      const uint32_t use = (uint32_t)(i >> 1);
+      // the fused z pass drains its one inverse accumulator (columns 256..) every tile
+      const int ab = ZZ ? 1 : (i & 1);
+      const uint32_t use = ZZ ? (uint32_t)i : (uint32_t)(i >> 1);
       const long long l = (long long)(blockIdx.x + i * gridDim.x) * 128 + q * 32 + lane;
       const bool valid = l < a.nlines;
       // output address of (line l, column 0) and the symbol's (x, y) part
       long long base = 0;
-      float sxy = 0.f;
+      float sxy = 1.f;
       if (valid) {
         base = out_base(o, l);
-        if (o.sym) {
+        if (o.sym || ZZ) {
           const int ry = (int)(l % a.Y), rx = (int)((l / a.Y) % a.X);
           sxy = a.gamma + a.alpha * (a.lx[rx] + a.ly[ry]);
+        }
+      }
+      bool conv_ok = true;
+      if constexpr (ZZ) {
+        // Scaled spectrum: block kb of the forward accumulator (columns 64 kb..) is read, divided
+        // by the symbol (gamma + alpha (lx + ly + lz))^2, split into bf16 hi/lo and written back
+        // in place as the inverse product's A operand: per 16 columns, 8 columns of hi pairs
+        // then 8 of lo pairs.  Block kb is converted by the four warps of part kb % nparts.
+        // A thread whose wait gives up skips the conversion but still reaches the drain's
+        // agreement below, where its part leaves together.
+        conv_ok = ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tfull[0]), (uint32_t)i & 1u, abort, a.poll);
+        ptx::tc_fence_after();
+        const uint32_t t1 = tmem + ((uint32_t)(q * 32) << 16);
+        for (int kb = part; conv_ok && kb < nkb; kb += nparts) {
+          const int c1 = min(4 * kb + 4, nch);
+          for (int c = 4 * kb; c < c1; ++c) {
+            float vc[16];
+            ptx::tmem_ld16(t1 + (uint32_t)(c * 16), vc);
+            uint32_t hw[8], lw[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              uint16_t h0, l0, h1, l1;
+              const int n = c * 16 + 2 * j;
+              const float d0 = fmaf(a.alpha, __ldg(a.lz + min(n, a.L - 1)), sxy);
+              const float d1 = fmaf(a.alpha, __ldg(a.lz + min(n + 1, a.L - 1)), sxy);
+              split1(__fdividef(vc[2 * j], d0 * d0), h0, l0);
+              split1(__fdividef(vc[2 * j + 1], d1 * d1), h1, l1);
+              hw[j] = pack_bf16x2(h0, h1);
+              lw[j] = pack_bf16x2(l0, l1);
+            }
+            ptx::tmem_st8(t1 + (uint32_t)(c * 16), hw);
+            if (a.split) ptx::tmem_st8(t1 + (uint32_t)(c * 16 + 8), lw);
+          }
+          ptx::tmem_wait_st();
+          ptx::tc_fence_before();
+          ptx::mbar_arrive(ptx::smem_u32(&b_a2[kb]));
         }
       }
       const long long line0 = l - lane;
@@ -549,8 +674,8 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
         load_old_rows(o, lane, line0, a.nlines, cbeg * 16, ncols, oldv);
         if (cbeg + 1 < cend) load_old_rows(o, lane, line0, a.nlines, cbeg * 16 + 16, ncols, oldv + 4);
       }
-      constexpr bool staged = EPI == EPI_T_STAGED;
-      int got = ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tfull[ab]), use & 1, abort, a.poll) ? 1 : 0;
+      constexpr bool staged = EPI == EPI_T_STAGED || ZZ;
+      int got = (conv_ok && ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tfull[ab]), use & 1, abort, a.poll)) ? 1 : 0;
       if constexpr (staged) {
         // the four warps of a column range meet at named barriers below: they give up together
         asm volatile(
@@ -562,7 +687,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
       }
       if (!got) break;
       ptx::tc_fence_after();
-      const uint32_t trow = tmem + (uint32_t)(ab * a.Nc) + ((uint32_t)(q * 32) << 16);
+      const uint32_t trow = tmem + (ZZ ? 256u : (uint32_t)(ab * a.Nc)) + ((uint32_t)(q * 32) << 16);
       if constexpr (staged) {
         // Transposed split output.  Per 16-column chunk the four quadrant warps of this column
         // range write their lines' hi/lo bf16 into the range's shared tile [plane][col][line];
@@ -734,9 +859,10 @@ cudaError_t ks_split_rows(const float* in, long long nrows, int L, int split, co
 
 // One pass of k_dft_ks over a split field `in` (hi plane, lo plane nlines*pitch elements later),
 // lines of length L along `axis` (0: x, 1: y, 2: z) with row pitch ks_pitch(L), output as `o`
-// says (eps: the update's step size for KS_OUT_UPD).
+// says (eps: the update's step size for KS_OUT_UPD).  zz: the fused z pass (axis 2): forward
+// product, symbol and inverse product of every line, output as the inverse pass's.
 cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, const void* in,
-                         long long nlines, const KsOut& o, float eps, cudaStream_t s) {
+                         long long nlines, const KsOut& o, float eps, cudaStream_t s, bool zz) {
   EncodeTiledFn enc = reinterpret_cast<EncodeTiledFn>(tma_encode_fn());
   if (!enc) return cudaErrorNotSupported;
   KsArgs a{};
@@ -759,11 +885,14 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
   a.X = kp.nx; a.Y = kp.ny;
   a.err = kp.err;
   a.poll = kp.poll_limit ? kp.poll_limit : (1u << 22);
+  a.zz = zz ? 1 : 0;
+  // the fused pass drains through the staging tiles: its output rows hold a multiple of 8 lines
+  if (zz && (axis != 2 || o.sym || !ks_staged(a))) return cudaErrorInvalidValue;
   const int P = ks_pitch(a.L);
   const int np = split ? 2 : 1;
   // A: [2 planes][nlines][P] bf16, box 64 k x 128 lines, 128-byte swizzle; k >= L and lines
   // beyond the field read as zero
-  CUtensorMap tmA, tmB;
+  CUtensorMap tmA, tmB, tmB2;
   {
     cuuint64_t dims[3] = {(cuuint64_t)a.L, (cuuint64_t)nlines, (cuuint64_t)np};
     cuuint64_t strides[2] = {(cuuint64_t)P * 2, (cuuint64_t)nlines * P * 2};
@@ -773,22 +902,25 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
-  // B: [2 planes][Nc][Kp] bf16 (zero padded), box 64 k x Nc rows
-  {
+  // B: [2 planes][Nc][Kp] bf16 (zero padded), box 64 k x Nc rows (the fused z pass: the forward
+  // table, then the inverse one)
+  for (int t = 0; t < (zz ? 2 : 1); ++t) {
     const int Kp = (a.L + 15) / 16 * 16;
     cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)a.Nc, 2};
     cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)a.Nc * Kp * 2};
     cuuint32_t box[3] = {64, (cuuint32_t)a.Nc, 1}, es[3] = {1, 1, 1};
-    if (enc(&tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, kp.ks[axis][inverse ? 1 : 0], dims,
+    const int which = zz ? t : (inverse ? 1 : 0);
+    if (enc(t ? &tmB2 : &tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, kp.ks[axis][which], dims,
             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
+  if (!zz) tmB2 = tmB;
   // Shared memory (<= 225 KB): B resident when all its k-blocks fit next to 2 A stages;
   // otherwise 3 A stages (2 when needed) and as many streamed B stages as fit (at least 2).
   const int budget = 225 * 1024 - 1024 - ks_tbytes(a) - ks_sbytes(a);
   const int ab = ks_abytes(split), bb = ks_bbytes(split, a.Nc);
-  if (a.nkb * bb + 2 * ab <= budget) {
+  if (!zz && a.nkb * bb + 2 * ab <= budget) {
     a.bres = 1;
     a.AS = min(KS_MAXS, (budget - a.nkb * bb) / ab);
     a.BS = 1;
@@ -807,6 +939,7 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
   auto kern = epi == EPI_T_STAGED ? k_dft_ks<EPI_T_STAGED>
             : epi == EPI_T        ? k_dft_ks<EPI_T>
             : epi == EPI_ROWS     ? k_dft_ks<EPI_ROWS>
+            : epi == EPI_ZZ       ? k_dft_ks<EPI_ZZ>
                                   : k_dft_ks<EPI_UPD>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -817,7 +950,7 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
     if (g_ks_sms <= 0) g_ks_sms = 148;
   }
   const int grid = a.ntiles < g_ks_sms ? a.ntiles : g_ks_sms;
-  if (grid > 0) kern<<<grid, KS_NT, smem, s>>>(tmA, tmB, a);
+  if (grid > 0) kern<<<grid, KS_NT, smem, s>>>(tmA, tmB, tmB2, a);
   return cudaGetLastError();
 }
 

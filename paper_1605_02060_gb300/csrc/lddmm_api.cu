@@ -158,7 +158,8 @@ Hook hook_of(lddmm_ctx* ctx) {
 const char* kernel_name(int kid) {
   static const char* names[KID_COUNT] = {"flow_back_disp", "flow_back_terms", "fwd_residual",
                                          "fwd_flow", "K_x_fwd", "K_y_fwd", "K_z_symbol",
-                                         "K_z_inv", "K_y_inv", "K_x_inv_update", "update", "ereg"};
+                                         "K_z_inv", "K_y_inv", "K_x_inv_update", "update", "ereg",
+                                         "K_z_fused"};
   return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 
