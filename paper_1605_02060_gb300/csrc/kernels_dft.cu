@@ -129,6 +129,7 @@ cudaError_t kplan_create(KPlan* kp, int nx, int ny, int nz, float hx, float hy, 
   for (int d = 0; d < 3; ++d) {
     std::vector<float> R, lam;
     real_dft_matrix(n[d], h[d], R, lam);
+    lam.resize((size_t)(n[d] + 15) / 16 * 16, 0.f);   // zero padded: 16-column groups load whole
     cudaError_t e;
     if ((e = upload(Rs[d], R)) != cudaSuccess) return e;
     if ((e = upload(ls[d], lam)) != cudaSuccess) return e;

@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
       ptx::mbar_init(ptx::smem_u32(&b_tempty[i]), 32 * nepi);
     }
     ptx::mbar_init(ptx::smem_u32(&b_fin), 1);
-    for (int i = 0; i < 4; ++i) ptx::mbar_init(ptx::smem_u32(&b_a2[i]), 128);
+    for (int i = 0; i < 4; ++i) ptx::mbar_init(ptx::smem_u32(&b_a2[i]), 32 * nepi);
     ptx::fence_mbar_init();
     abort_sh = 0;
   }
@@ -346,12 +346,14 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
   const int nkb = a.nkb, AS = a.AS, BS = a.BS;
 
   if (warp == KS_W_TMA) {
-    // ------------------------------------------------------------ producer
+    // ------------------------------------------------------------ producers
+    // lane 0 loads the A boxes (and a resident B once); lane 1 streams B, so that neither ring's
+    // refill waits behind the other's
+    const int np = a.split ? 2 : 1;
     if (lane == 0) {
       ptx::prefetch_tmap(&tmA);
       ptx::prefetch_tmap(&tmB);
       if (ZZ) ptx::prefetch_tmap(&tmB2);
-      const int np = a.split ? 2 : 1;
       if (a.bres && my_tiles > 0) {
         const uint32_t fb = ptx::smem_u32(&b_bfull[0]);
         ptx::mbar_arrive_expect_tx(fb, (uint32_t)(nkb * bbytes));
@@ -360,51 +362,44 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
             ptx::tma_load_3d(ptx::smem_u32(bring + kb * bbytes + pl * a.Nc * 128), &tmB, kb * 64,
                              0, pl, fb);
       }
-      uint32_t g = 0, gb = 0;
+      uint32_t g = 0;
       for (int i = 0; i < my_tiles; ++i) {
         const int line0 = (blockIdx.x + i * gridDim.x) * 128;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = (int)(g % AS);
-          if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_aempty[s]), ((g / AS) & 1) ^ 1, abort, a.poll)) goto p_done;
+          if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_aempty[s]), ((g / AS) & 1) ^ 1, abort, a.poll)) goto pa_done;
           const uint32_t fa = ptx::smem_u32(&b_afull[s]);
           ptx::mbar_arrive_expect_tx(fa, (uint32_t)abytes);
           for (int pl = 0; pl < np; ++pl)
             ptx::tma_load_3d(ptx::smem_u32(aring + s * abytes + pl * KS_ABOX), &tmA, kb * 64,
                              line0, pl, fa);
-          if (!a.bres) {
-            const int sb = (int)(gb % BS);
-            if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bempty[sb]), ((gb / BS) & 1) ^ 1, abort, a.poll)) { ++g; goto p_done; }
-            const uint32_t fb = ptx::smem_u32(&b_bfull[sb]);
-            ptx::mbar_arrive_expect_tx(fb, (uint32_t)bbytes);
-            for (int pl = 0; pl < np; ++pl)
-              ptx::tma_load_3d(ptx::smem_u32(bring + sb * bbytes + pl * a.Nc * 128), &tmB,
-                               kb * 64, 0, pl, fb);
-            ++gb;
-          }
-        }
-        // the fused z pass streams the inverse table after the forward one, block by block
-        if (ZZ) {
-          for (int kb = 0; kb < nkb; ++kb) {
-            const int sb = (int)(gb % BS);
-            if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bempty[sb]), ((gb / BS) & 1) ^ 1, abort, a.poll)) goto p_done;
-            const uint32_t fb = ptx::smem_u32(&b_bfull[sb]);
-            ptx::mbar_arrive_expect_tx(fb, (uint32_t)bbytes);
-            for (int pl = 0; pl < np; ++pl)
-              ptx::tma_load_3d(ptx::smem_u32(bring + sb * bbytes + pl * a.Nc * 128), &tmB2,
-                               kb * 64, 0, pl, fb);
-            ++gb;
-          }
         }
       }
-    p_done:
+    pa_done:
       // copies still in flight (only after an abort can any remain unconsumed)
       for (uint32_t q = (g > (uint32_t)AS ? g - AS : 0u); q < g; ++q)
         ptx::mbar_wait(ptx::smem_u32(&b_afull[q % AS]), (q / AS) & 1);
-      if (!a.bres)
-        for (uint32_t q = (gb > (uint32_t)BS ? gb - BS : 0u); q < gb; ++q)
-          ptx::mbar_wait(ptx::smem_u32(&b_bfull[q % BS]), (q / BS) & 1);
-      else if (my_tiles > 0)
-        ptx::mbar_wait(ptx::smem_u32(&b_bfull[0]), 0u);
+      if (a.bres && my_tiles > 0) ptx::mbar_wait(ptx::smem_u32(&b_bfull[0]), 0u);
+    } else if (lane == 1 && !a.bres) {
+      // the tiles' B blocks in the order the MMA takes them (the fused z pass: the forward
+      // table's blocks, then the inverse table's)
+      uint32_t gb = 0;
+      for (int i = 0; i < my_tiles; ++i) {
+        for (int t = 0; t < (ZZ ? 2 : 1); ++t) {
+          for (int kb = 0; kb < nkb; ++kb, ++gb) {
+            const int sb = (int)(gb % BS);
+            if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_bempty[sb]), ((gb / BS) & 1) ^ 1, abort, a.poll)) goto pb_done;
+            const uint32_t fb = ptx::smem_u32(&b_bfull[sb]);
+            ptx::mbar_arrive_expect_tx(fb, (uint32_t)bbytes);
+            for (int pl = 0; pl < np; ++pl)
+              ptx::tma_load_3d(ptx::smem_u32(bring + sb * bbytes + pl * a.Nc * 128),
+                               t ? &tmB2 : &tmB, kb * 64, 0, pl, fb);
+          }
+        }
+      }
+    pb_done:
+      for (uint32_t q = (gb > (uint32_t)BS ? gb - BS : 0u); q < gb; ++q)
+        ptx::mbar_wait(ptx::smem_u32(&b_bfull[q % BS]), (q / BS) & 1);
     }
   } else if (warp == KS_W_MMA) {
     // ------------------------------------------------------------ MMA issuer
@@ -626,28 +621,37 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
         // Scaled spectrum: block kb of the forward accumulator (columns 64 kb..) is read, divided
         // by the symbol (gamma + alpha (lx + ly + lz))^2, split into bf16 hi/lo and written back
         // in place as the inverse product's A operand: per 16 columns, 8 columns of hi pairs
-        // then 8 of lo pairs.  Block kb is converted by the four warps of part kb % nparts.
-        // A thread whose wait gives up skips the conversion but still reaches the drain's
-        // agreement below, where its part leaves together.
+        // then 8 of lo pairs.  The 16-column chunks go round robin to the parts (chunk c to part
+        // c % nparts), block by block; every epilogue thread arrives once per block, so block kb
+        // is ready as soon as its few chunks are.  A thread whose wait gives up skips the
+        // conversion but still reaches the drain's agreement below, where its part leaves
+        // together.  (lz is zero padded to whole 16-column groups.)
         conv_ok = ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tfull[0]), (uint32_t)i & 1u, abort, a.poll);
         ptx::tc_fence_after();
         const uint32_t t1 = tmem + ((uint32_t)(q * 32) << 16);
-        for (int kb = part; conv_ok && kb < nkb; kb += nparts) {
+        for (int kb = 0; conv_ok && kb < nkb; ++kb) {
           const int c1 = min(4 * kb + 4, nch);
           for (int c = 4 * kb; c < c1; ++c) {
+            if (c % nparts != part) continue;
             float vc[16];
             ptx::tmem_ld16(t1 + (uint32_t)(c * 16), vc);
+            const float4* lz4 = reinterpret_cast<const float4*>(a.lz + c * 16);
             uint32_t hw[8], lw[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              uint16_t h0, l0, h1, l1;
-              const int n = c * 16 + 2 * j;
-              const float d0 = fmaf(a.alpha, __ldg(a.lz + min(n, a.L - 1)), sxy);
-              const float d1 = fmaf(a.alpha, __ldg(a.lz + min(n + 1, a.L - 1)), sxy);
-              split1(__fdividef(vc[2 * j], d0 * d0), h0, l0);
-              split1(__fdividef(vc[2 * j + 1], d1 * d1), h1, l1);
-              hw[j] = pack_bf16x2(h0, h1);
-              lw[j] = pack_bf16x2(l0, l1);
+            for (int j4 = 0; j4 < 4; ++j4) {
+              const float4 z4 = __ldg(lz4 + j4);
+              const float zl[4] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+              for (int jj = 0; jj < 2; ++jj) {
+                const int j = 2 * j4 + jj;
+                uint16_t h0, l0, h1, l1;
+                const float d0 = fmaf(a.alpha, zl[2 * jj], sxy);
+                const float d1 = fmaf(a.alpha, zl[2 * jj + 1], sxy);
+                split1(__fdividef(vc[2 * j], d0 * d0), h0, l0);
+                split1(__fdividef(vc[2 * j + 1], d1 * d1), h1, l1);
+                hw[j] = pack_bf16x2(h0, h1);
+                lw[j] = pack_bf16x2(l0, l1);
+              }
             }
             ptx::tmem_st8(t1 + (uint32_t)(c * 16), hw);
             if (a.split) ptx::tmem_st8(t1 + (uint32_t)(c * 16 + 8), lw);
