@@ -138,11 +138,9 @@ struct KPlan {
   // nk = Npad/16 k-steps, each [hi | lo] bf16 blocks of Npad x 16 in K-major core-matrix order
   uint16_t* tc[3][2];
   // operand tables of the pre-split pass (kernels_ks.cu) per axis and direction: bf16
-  // [2][Nc][Kp] (hi plane, lo plane), row n = output column (Nc = min(256, ceil16(n))), k
-  // contiguous (Kp = ceil16(n)), zero beyond the axis length; for 256 < nx <= 264 the x
-  // columns 256.. as float [ceil64(nx)][8] (kstail, zero padded)
+  // [2][Nc][Kp] (hi plane, lo plane), row n = output column, k contiguous (Nc = Kp =
+  // ceil16(n)), zero beyond the axis length
   uint16_t* ks[3][2];
-  float* kstail[2];
   int* err;  // device flag set by a tensor-core kernel whose bounded wait timed out
   // probes per pipeline wait in the pre-split tensor-core pass (0: the default, 2^22)
   uint32_t poll_limit;

@@ -84,10 +84,10 @@ static void tc_table(const std::vector<float>& R, int n, bool inverse, int rows,
 }
 
 // Operand table of the pre-split pass: B(k, n) as bf16 [hi plane][lo plane], each [Nc][Kp]
-// row-major (row n = output column, k contiguous), Nc = min(256, ceil16(n)), Kp = ceil16(n),
-// zero for n >= n_len or k >= n_len.
+// row-major (row n = output column, k contiguous), Nc = Kp = ceil16(n), zero for n >= n_len or
+// k >= n_len.
 static void ks_table(const std::vector<float>& R, int n, bool inverse, std::vector<uint16_t>& t) {
-  const int Kp = (n + 15) / 16 * 16, Nc = Kp < 256 ? Kp : 256;
+  const int Kp = (n + 15) / 16 * 16, Nc = Kp;
   const size_t plane = (size_t)Nc * Kp;
   t.assign(2 * plane, 0);
   for (int row = 0; row < n && row < Nc; ++row)
@@ -96,17 +96,6 @@ static void ks_table(const std::vector<float>& R, int n, bool inverse, std::vect
       const uint16_t bh = bf16_rn(b);
       t[(size_t)row * Kp + k] = bh;
       t[plane + (size_t)row * Kp + k] = bf16_rn(b - bf16_to_f(bh));
-    }
-}
-
-// Columns 256..n-1 (at most 8) of B for the pre-split x pass, float [ceil64(n)][8].
-static void ks_tail_table(const std::vector<float>& R, int n, bool inverse, std::vector<float>& t) {
-  const int rows = (n + 63) / 64 * 64;
-  t.assign((size_t)rows * 8, 0.f);
-  for (int k = 0; k < n; ++k)
-    for (int j = 0; j < 8 && 256 + j < n; ++j) {
-      const int col = 256 + j;
-      t[(size_t)k * 8 + j] = inverse ? R[(size_t)k * n + col] : R[(size_t)col * n + k];
     }
 }
 
@@ -143,11 +132,6 @@ cudaError_t kplan_create(KPlan* kp, int nx, int ny, int nz, float hx, float hy, 
         std::vector<uint16_t> t;
         ks_table(R, n[d], dir == 1, t);
         if ((e = upload(&kp->ks[d][dir], t)) != cudaSuccess) return e;
-        if (d == 0 && n[d] > 256) {
-          std::vector<float> tt;
-          ks_tail_table(R, n[d], dir == 1, tt);
-          if ((e = upload(&kp->kstail[dir], tt)) != cudaSuccess) return e;
-        }
       }
     }
   }
@@ -166,7 +150,6 @@ void kplan_destroy(KPlan* kp) {
   for (int dir = 0; dir < 2; ++dir) {
     for (int d = 0; d < 3; ++d)
       if (kp->ks[d][dir]) cudaFree(kp->ks[d][dir]);
-    if (kp->kstail[dir]) cudaFree(kp->kstail[dir]);
   }
   *kp = KPlan{};
 }

@@ -43,23 +43,24 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 constexpr int KS_NT = 448;
-constexpr int KS_W_TMA = 0, KS_W_MMA = 1, KS_W_TAIL = 10;
-constexpr int KS_NEPI = 8;                 // epilogue warps 2..9 (the staged outputs of the
-                                           // passes without FP32 tail columns: 2..13)
-constexpr int KS_NTAIL = 128;              // tail threads (warps 10..13)
+constexpr int KS_W_TMA = 0, KS_W_MMA = 1;  // epilogue: warps 2 .. 2 + 4 nparts - 1
 constexpr int KS_ABOX = 128 * 128;         // one A box: 128 lines x 64 bf16 (16 KB)
 constexpr int KS_MAXS = 6;                 // ring depths (A and streamed B) at most
+// Lines longer than 256 (up to 272): the main product covers the output columns 0..239 (N = 240,
+// two accumulators at TMEM columns 0 and 240) and a second product the columns 240.. (N = 32)
+// into one accumulator at TMEM column 480, which the epilogue drains first in every tile.
+constexpr int KS_NMAIN = 240, KS_TCOL = 480;
 
 struct KsArgs {
   int nlines;          // lines of the input field
   int L;               // transform length: valid k and valid output columns
-  int Nc;              // output columns on the tensor cores (L rounded up to 16, at most 256)
+  int Nc;              // output columns (L rounded up to 16, at most 272): B has Nc rows
+  int Nm, Nt;          // widths of the main and the second product (Nc and 0, or 240 and Nc - 240)
   int nk, nkb;         // 16-wide k-steps and 64-wide k-blocks over the whole length
   int split;           // 1: three products (hi*hi + hi*lo + lo*hi), 0: hi*hi
   int AS, BS, bres;    // A ring depth; streamed B ring depth; 1: B resident (nkb blocks)
   int ntiles;          // 128-line tiles
-  int tw;              // FP32 tail columns 256..256+tw-1 (x axis longer than 256), else 0
-  const float* tail;   // their table B(k, 256 + j) as float [nkb * 64][8], zero padded
+  int nparts;          // epilogue column ranges (four warps each, one per TMEM lane quadrant)
   KsOut o;             // output addressing
   float eps;           // KS_OUT_UPD: step size
   const float* lx;     // symbol (o.sym): lambda per x, y, z frequency
@@ -74,7 +75,6 @@ struct KsArgs {
 
 __host__ __device__ inline int ks_abytes(int split) { return (split ? 2 : 1) * KS_ABOX; }
 __host__ __device__ inline int ks_bbytes(int split, int Nc) { return (split ? 2 : 1) * Nc * 128; }
-__host__ __device__ inline int ks_tbytes(const KsArgs& a) { return a.tw ? a.nkb * 64 * 8 * 4 : 0; }
 // per epilogue warp: 32 lines x 16 columns of fp32, rows padded to 17 (conflict-free transpose)
 constexpr int KS_SROW = 17;
 // transposed split outputs: per column range (2 or 3 of them), a tile of 16 columns x 128 lines
@@ -86,19 +86,16 @@ constexpr int KS_CTILE = 2 * 16 * 128 * 2;
 __host__ __device__ inline bool ks_staged(const KsArgs& a) {
   return a.o.G != 1 && a.o.kind == KS_OUT_SPLIT && a.o.E % 8 == 0;
 }
-// Passes without FP32 tail columns whose outputs are staged (row outputs, or transposed ones
-// with aligned pieces) run 12 epilogue warps, three per TMEM lane quadrant; the others 8.
-__host__ __device__ inline int ks_nparts(const KsArgs& a) {
-  return (a.tw == 0 && (ks_staged(a) || a.o.G == 1)) ? 3 : 2;
-}
 __host__ __device__ inline int ks_sbytes(const KsArgs& a) {
-  if (a.o.G == 1) return 4 * ks_nparts(a) * 32 * KS_SROW * 4;   // row outputs: a tile per warp
-  return ks_staged(a) ? ks_nparts(a) * KS_CTILE : 0;
+  if (a.o.G == 1) return 4 * a.nparts * 32 * KS_SROW * 4;   // row outputs: a tile per warp
+  return ks_staged(a) ? a.nparts * KS_CTILE : 0;
 }
 __host__ __device__ inline int ks_smem(const KsArgs& a) {
   return 1024 + a.AS * ks_abytes(a.split) + (a.bres ? a.nkb : a.BS) * ks_bbytes(a.split, a.Nc) +
-         ks_tbytes(a) + ks_sbytes(a);
+         ks_sbytes(a);
 }
+// rows of one B box (the TMA box is at most 256 rows: a 272-row table takes two)
+__host__ __device__ inline int ks_brows(int Nc) { return Nc <= 256 ? Nc : Nc / 2; }
 
 // tcgen05 shared-memory descriptor for a K-major operand in the 128-byte swizzled layout:
 // rows of 128 bytes (64 bf16 of k), 8-row atoms of 1024 bytes (SBO), atoms 1024-byte aligned;
@@ -299,20 +296,18 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
   // inverse accumulator drained, b_a2[kb] = 64-column block kb of the scaled spectrum (the second
   // product's A operand, in TMEM over the forward accumulator) converted
   __shared__ __align__(8) uint64_t b_a2[4];
+  // the second product's accumulator (columns 240..) drained by the last epilogue part
+  __shared__ __align__(8) uint64_t b_ttail;
   __shared__ uint32_t tmem_sh;
   __shared__ int abort_sh;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // epilogue warps: 2..9, and 10..13 as well when they have no tail columns to compute and the
-  // outputs are staged
-  const bool wide = ks_nparts(a) == 3;
-  const int nepi = wide ? 12 : KS_NEPI;
+  const int nepi = 4 * a.nparts;                   // epilogue warps 2 .. 2 + nepi - 1
   uint8_t* smem = smem_dyn + ((1024u - (ptx::smem_u32(smem_dyn) & 1023u)) & 1023u);
   const int abytes = ks_abytes(a.split), bbytes = ks_bbytes(a.split, a.Nc);
   uint8_t* aring = smem;
   uint8_t* bring = smem + a.AS * abytes;
-  float* ttab = reinterpret_cast<float*>(bring + (a.bres ? a.nkb : a.BS) * bbytes);
-  float* stg = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(ttab) + ks_tbytes(a));
+  float* stg = reinterpret_cast<float*>(bring + (a.bres ? a.nkb : a.BS) * bbytes);
   volatile int* abort = &abort_sh;
 
   if (warp == KS_W_MMA) {
@@ -322,7 +317,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
   if (threadIdx.x == 0) {
     for (int i = 0; i < a.AS; ++i) {
       ptx::mbar_init(ptx::smem_u32(&b_afull[i]), 1);
-      ptx::mbar_init(ptx::smem_u32(&b_aempty[i]), 1 + (a.tw ? KS_NTAIL : 0));
+      ptx::mbar_init(ptx::smem_u32(&b_aempty[i]), 1);
     }
     for (int i = 0; i < KS_MAXS; ++i) {
       ptx::mbar_init(ptx::smem_u32(&b_bfull[i]), 1);
@@ -334,6 +329,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
     }
     ptx::mbar_init(ptx::smem_u32(&b_fin), 1);
     for (int i = 0; i < 4; ++i) ptx::mbar_init(ptx::smem_u32(&b_a2[i]), 32 * nepi);
+    ptx::mbar_init(ptx::smem_u32(&b_ttail), 128);
     ptx::fence_mbar_init();
     abort_sh = 0;
   }
@@ -350,6 +346,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
     // lane 0 loads the A boxes (and a resident B once); lane 1 streams B, so that neither ring's
     // refill waits behind the other's
     const int np = a.split ? 2 : 1;
+    const int br = ks_brows(a.Nc);
     if (lane == 0) {
       ptx::prefetch_tmap(&tmA);
       ptx::prefetch_tmap(&tmB);
@@ -359,8 +356,9 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
         ptx::mbar_arrive_expect_tx(fb, (uint32_t)(nkb * bbytes));
         for (int kb = 0; kb < nkb; ++kb)
           for (int pl = 0; pl < np; ++pl)
-            ptx::tma_load_3d(ptx::smem_u32(bring + kb * bbytes + pl * a.Nc * 128), &tmB, kb * 64,
-                             0, pl, fb);
+            for (int r = 0; r < a.Nc; r += br)
+              ptx::tma_load_3d(ptx::smem_u32(bring + kb * bbytes + (pl * a.Nc + r) * 128), &tmB,
+                               kb * 64, r, pl, fb);
       }
       uint32_t g = 0;
       for (int i = 0; i < my_tiles; ++i) {
@@ -392,8 +390,9 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
             const uint32_t fb = ptx::smem_u32(&b_bfull[sb]);
             ptx::mbar_arrive_expect_tx(fb, (uint32_t)bbytes);
             for (int pl = 0; pl < np; ++pl)
-              ptx::tma_load_3d(ptx::smem_u32(bring + sb * bbytes + pl * a.Nc * 128),
-                               t ? &tmB2 : &tmB, kb * 64, 0, pl, fb);
+              for (int r = 0; r < a.Nc; r += br)
+                ptx::tma_load_3d(ptx::smem_u32(bring + sb * bbytes + (pl * a.Nc + r) * 128),
+                                 t ? &tmB2 : &tmB, kb * 64, r, pl, fb);
           }
         }
       }
@@ -404,9 +403,11 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
   } else if (warp == KS_W_MMA) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t id = ptx::idesc_bf16(128, a.Nc);
+      const uint32_t id = ptx::idesc_bf16(128, a.Nm);
+      const uint32_t idt = a.Nt ? ptx::idesc_bf16(128, a.Nt) : 0u;
       const uint32_t a0 = ptx::smem_u32(aring), b0 = ptx::smem_u32(bring);
       const uint32_t blo = (uint32_t)a.Nc * 128u;               // B lo plane offset
+      const uint32_t bto = (uint32_t)a.Nm * 128u;               // the second product's B rows
       uint32_t g = 0;
       if constexpr (ZZ) {
         // forward product into columns 0.. (A from the ring, B the forward table), then, block by
@@ -480,7 +481,8 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
         const uint32_t use = (uint32_t)(i >> 1);
         if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tempty[ab]), (use & 1) ^ 1, abort, a.poll)) break;
         ptx::tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(ab * a.Nc);
+        const uint32_t d = tmem + (uint32_t)(ab * (a.Nt ? KS_NMAIN : a.Nc));
+        const uint32_t dt = tmem + (uint32_t)KS_TCOL;
         bool ok = true;
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = (int)(g % AS);
@@ -503,6 +505,26 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
               ptx::mma_bf16(d, dAl, dBh, id, 1u);
             }
           }
+          if (a.Nt) {
+            // the columns 240..: the epilogue drains the previous tile's first, before this
+            // tile's second product starts
+            if (kb == 0 && i > 0 &&
+                !ptx::mbar_wait_or_abort(ptx::smem_u32(&b_ttail), (uint32_t)(i - 1) & 1u, abort, a.poll)) {
+              ok = false;
+              break;
+            }
+            ptx::tc_fence_after();
+            for (int j = 0; j < nst; ++j) {
+              const uint64_t dAh = desc_sw128(as + 32u * j), dBh = desc_sw128(bs + bto + 32u * j);
+              ptx::mma_bf16(dt, dAh, dBh, idt, (kb | j) ? 1u : 0u);
+              if (a.split) {
+                const uint64_t dAl = desc_sw128(as + (uint32_t)KS_ABOX + 32u * j);
+                const uint64_t dBl = desc_sw128(bs + blo + bto + 32u * j);
+                ptx::mma_bf16(dt, dAh, dBl, idt, 1u);
+                ptx::mma_bf16(dt, dAl, dBh, idt, 1u);
+              }
+            }
+          }
           ptx::mma_commit(ptx::smem_u32(&b_aempty[s]));
           if (!a.bres) ptx::mma_commit(ptx::smem_u32(&b_bempty[sb]));
         }
@@ -512,89 +534,20 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
     m_done:
       ptx::mma_commit(ptx::smem_u32(&b_fin));
     }
-  } else if (warp >= KS_W_TAIL && !wide) {
-    // ------------------------------------------------------------ FP32 tail columns
-    if (a.tw) {
-      const int m = threadIdx.x - KS_W_TAIL * 32;             // line of the tile
-      const float4* gt = reinterpret_cast<const float4*>(a.tail);
-      float4* st = reinterpret_cast<float4*>(ttab);
-      for (int q = m; q < nkb * 64 * 2; q += KS_NTAIL) st[q] = __ldg(gt + q);
-      asm volatile("bar.sync 1, %0;" ::"n"(KS_NTAIL) : "memory");
-      const int sw = m & 7;
-      uint32_t g = 0;
-      bool ok = true;
-      for (int i = 0; i < my_tiles && ok; ++i) {
-        const long long l = (long long)(blockIdx.x + i * gridDim.x) * 128 + m;
-        // the update: the old v of the tail columns (row l at l * P) is loaded into registers
-        // before the products, so its latency passes while the k-blocks are summed
-        float oldt[8];
-        if constexpr (EPI == EPI_UPD) {
-          const bool bf = a.o.kind == KS_OUT_UPD_BF16;
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            oldt[j] = 0.f;
-            if (l < a.nlines && j < a.tw) {
-              const long long off = l * a.o.P + 256 + j;
-              oldt[j] = bf ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(a.o.out)[off])
-                           : reinterpret_cast<const float*>(a.o.out)[off];
-            }
-          }
-        }
-        float acc[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j] = 0.f;
-        for (int kb = 0; kb < nkb; ++kb, ++g) {
-          const int s = (int)(g % AS);
-          if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_afull[s]), (g / AS) & 1, abort, a.poll)) { ok = false; break; }
-          // row m of the swizzled box: 16-byte chunk c (8 k values) stored at chunk c ^ (m % 8)
-          const uint8_t* hrow = aring + s * abytes + m * 128;
-          for (int c = 0; c < 8; ++c) {
-            float x[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) x[j] = 0.f;
-            add_bf8(*reinterpret_cast<const uint4*>(hrow + ((c ^ sw) << 4)), x);
-            if (a.split) add_bf8(*reinterpret_cast<const uint4*>(hrow + KS_ABOX + ((c ^ sw) << 4)), x);
-            const float4* tr = st + (kb * 64 + c * 8) * 2;
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-              const float4 t0 = tr[2 * kk], t1 = tr[2 * kk + 1];
-              acc[0] = fmaf(x[kk], t0.x, acc[0]);
-              acc[1] = fmaf(x[kk], t0.y, acc[1]);
-              acc[2] = fmaf(x[kk], t0.z, acc[2]);
-              acc[3] = fmaf(x[kk], t0.w, acc[3]);
-              acc[4] = fmaf(x[kk], t1.x, acc[4]);
-              acc[5] = fmaf(x[kk], t1.y, acc[5]);
-              acc[6] = fmaf(x[kk], t1.z, acc[6]);
-              acc[7] = fmaf(x[kk], t1.w, acc[7]);
-            }
-          }
-          ptx::mbar_arrive(ptx::smem_u32(&b_aempty[s]));
-        }
-        if (!ok) break;
-        if (l < a.nlines) {
-          if constexpr (EPI == EPI_UPD) {
-            const bool bf = a.o.kind == KS_OUT_UPD_BF16;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              if (j < a.tw) {
-                const long long off = l * a.o.P + 256 + j;
-                const float r = oldt[j] - a.eps * (2.f * oldt[j] - acc[j]);
-                if (bf) reinterpret_cast<__nv_bfloat16*>(a.o.out)[off] = __float2bfloat16_rn(r);
-                else reinterpret_cast<float*>(a.o.out)[off] = r;
-              }
-            }
-          } else {
-            store_scalar<8>(a.o, a.split, out_base(a.o, l), 256, acc, a.tw);
-          }
-        }
-      }
-    }
-  } else {
+  } else if (warp < 2 + nepi) {
     // ------------------------------------------------------------ epilogue (warps 2-9 or 2-13)
     const int q = warp & 3;                          // TMEM lane quadrant of this warp
     const int part = (warp - 2) >> 2, nparts = nepi >> 2;   // column range of this warp
     const int nch = a.Nc / 16;
     const int cbeg = part * nch / nparts, cend = (part + 1) * nch / nparts;
+    // This part's chunks in the order it drains them: the second product's (columns 240.., in
+    // the last part) first, so that the next tile's second product may start, then the main
+    // product's.  Chunk c lies at TMEM column 16 c of the accumulator, or 480 + 16 (c - 15).
+    const int ntm = a.Nt ? KS_NMAIN / 16 : nch;      // chunks of the main product
+    const int tb = cend > ntm ? max(cbeg, ntm) : cend;
+    const int ntl = cend - tb;                       // second-product chunks of this part
+    const int cnt = cend - cbeg;
+    auto chunk_at = [&](int k) { return k < ntl ? tb + k : cbeg + (k - ntl); };
     const KsOut& o = a.o;
     const int Lc = min(a.L, a.Nc);                   // valid tensor-core output columns
     // columns written per line (row-wise split outputs stop at the row pitch)
@@ -672,11 +625,12 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
                             (uint32_t)((c1 - cbeg * 16) * es));
       }
       // the update: the old v of the first pair of chunks is requested before the wait for the
-      // accumulator, each later pair's just before its TMEM load
+      // accumulator, each later pair's just before its TMEM load (pairs never straddle the two
+      // products: a part holds 0 or 2 chunks of the second)
       float4 oldv[8];
-      if (EPI == EPI_UPD && cbeg < cend) {
-        load_old_rows(o, lane, line0, a.nlines, cbeg * 16, ncols, oldv);
-        if (cbeg + 1 < cend) load_old_rows(o, lane, line0, a.nlines, cbeg * 16 + 16, ncols, oldv + 4);
+      if (EPI == EPI_UPD && cnt > 0) {
+        load_old_rows(o, lane, line0, a.nlines, chunk_at(0) * 16, ncols, oldv);
+        if (cnt > 1) load_old_rows(o, lane, line0, a.nlines, chunk_at(1) * 16, ncols, oldv + 4);
       }
       constexpr bool staged = EPI == EPI_T_STAGED || ZZ;
       int got = (conv_ok && ptx::mbar_wait_or_abort(ptx::smem_u32(&b_tfull[ab]), use & 1, abort, a.poll)) ? 1 : 0;
@@ -691,7 +645,11 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
       }
       if (!got) break;
       ptx::tc_fence_after();
-      const uint32_t trow = tmem + (ZZ ? 256u : (uint32_t)(ab * a.Nc)) + ((uint32_t)(q * 32) << 16);
+      const uint32_t tlane = tmem + ((uint32_t)(q * 32) << 16);
+      const uint32_t tbuf = ZZ ? 256u : (uint32_t)(ab * (a.Nt ? KS_NMAIN : a.Nc));
+      auto tcol = [&](int c) -> uint32_t {
+        return tlane + (c < ntm ? tbuf + 16u * (uint32_t)c : (uint32_t)KS_TCOL + 16u * (uint32_t)(c - ntm));
+      };
       if constexpr (staged) {
         // Transposed split output.  Per 16-column chunk the four quadrant warps of this column
         // range write their lines' hi/lo bf16 into the range's shared tile [plane][col][line];
@@ -711,9 +669,14 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
         const int kcut = run ? 8 : (int)min((long long)8, o.E - lg0 % o.E);
         const long long nb = (!run && lg0 + kcut < a.nlines) ? out_base(o, lg0 + kcut) : 0;
         const int np = a.split ? 2 : 1;
-        for (int c = cbeg; c < cend; ++c) {
+        for (int k = 0; k < cnt; ++k) {
+          const int c = chunk_at(k);
           float vc[16];
-          ptx::tmem_ld16(trow + (uint32_t)(c * 16), vc);
+          ptx::tmem_ld16(tcol(c), vc);
+          if (k + 1 == ntl) {             // the second product's columns are read
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(ptx::smem_u32(&b_ttail));
+          }
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             uint16_t h, lo;
@@ -751,15 +714,20 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
           asm volatile("bar.sync %0, 128;" ::"r"(2 + part) : "memory");
         }
       } else {
-      for (int cp = cbeg; cp < cend; cp += 2) {
-        const int npair = min(2, cend - cp);
-        if (EPI == EPI_UPD && cp > cbeg) {
+      for (int k = 0; k < cnt; k += 2) {
+        const int cp = chunk_at(k);
+        const int npair = (k + 1 < cnt && k + 1 != ntl) ? 2 : 1;
+        if (EPI == EPI_UPD && k > 0) {
           load_old_rows(o, lane, line0, a.nlines, cp * 16, ncols, oldv);
           if (npair == 2) load_old_rows(o, lane, line0, a.nlines, cp * 16 + 16, ncols, oldv + 4);
         }
         float v[32];
-        if (npair == 2) ptx::tmem_ld32(trow + (uint32_t)(cp * 16), v);
-        else ptx::tmem_ld16(trow + (uint32_t)(cp * 16), *reinterpret_cast<float(*)[16]>(v));
+        if (npair == 2) ptx::tmem_ld32(tcol(cp), v);
+        else ptx::tmem_ld16(tcol(cp), *reinterpret_cast<float(*)[16]>(v));
+        if (k + npair == ntl) {           // the second product's columns are read
+          ptx::tc_fence_before();
+          ptx::mbar_arrive(ptx::smem_u32(&b_ttail));
+        }
 #pragma unroll
         for (int u2 = 0; u2 < 2; ++u2) {
           if (u2 >= npair) break;
@@ -840,7 +808,6 @@ int ks_pitch(int L) { return (L + 7) / 8 * 8; }
 
 bool ks_supported(const KPlan& kp) {
   if (!tma_encode_fn() || !kp.ks[0][0] || !kp.ks[1][0] || !kp.ks[2][0]) return false;
-  if (kp.nx > 256 && !kp.kstail[0]) return false;
   return kp.nx % 4 == 0 && kp.nx <= 264 && kp.ny <= 256 && kp.nz <= 256;
 }
 
@@ -871,12 +838,12 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
   if (!enc) return cudaErrorNotSupported;
   KsArgs a{};
   a.L = axis == 0 ? kp.nx : axis == 1 ? kp.ny : kp.nz;
-  a.Nc = min(256, (a.L + 15) / 16 * 16);
-  a.tw = a.L > 256 ? a.L - 256 : 0;
-  if (a.tw > 8) return cudaErrorNotSupported;
+  a.Nc = (a.L + 15) / 16 * 16;
+  if (a.Nc > 272) return cudaErrorNotSupported;
+  a.Nm = a.Nc <= 256 ? a.Nc : KS_NMAIN;
+  a.Nt = a.Nc - a.Nm;
   a.nk = (a.L + 15) / 16;
   a.nkb = (a.L + 63) / 64;
-  a.tail = a.tw ? kp.kstail[inverse ? 1 : 0] : nullptr;
   a.split = split;
   a.nlines = (int)nlines;
   a.ntiles = (int)((nlines + 127) / 128);
@@ -891,7 +858,7 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
   a.poll = kp.poll_limit ? kp.poll_limit : (1u << 22);
   a.zz = zz ? 1 : 0;
   // the fused pass drains through the staging tiles: its output rows hold a multiple of 8 lines
-  if (zz && (axis != 2 || o.sym || !ks_staged(a))) return cudaErrorInvalidValue;
+  if (zz && (axis != 2 || o.sym || !ks_staged(a) || a.Nt)) return cudaErrorInvalidValue;
   const int P = ks_pitch(a.L);
   const int np = split ? 2 : 1;
   // A: [2 planes][nlines][P] bf16, box 64 k x 128 lines, 128-byte swizzle; k >= L and lines
@@ -906,13 +873,13 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return cudaErrorInvalidValue;
   }
-  // B: [2 planes][Nc][Kp] bf16 (zero padded), box 64 k x Nc rows (the fused z pass: the forward
-  // table, then the inverse one)
+  // B: [2 planes][Nc][Kp] bf16 (zero padded), box 64 k x Nc rows (two boxes of Nc / 2 rows past
+  // 256; the fused z pass: the forward table, then the inverse one)
   for (int t = 0; t < (zz ? 2 : 1); ++t) {
     const int Kp = (a.L + 15) / 16 * 16;
     cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)a.Nc, 2};
     cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)a.Nc * Kp * 2};
-    cuuint32_t box[3] = {64, (cuuint32_t)a.Nc, 1}, es[3] = {1, 1, 1};
+    cuuint32_t box[3] = {64, (cuuint32_t)ks_brows(a.Nc), 1}, es[3] = {1, 1, 1};
     const int which = zz ? t : (inverse ? 1 : 0);
     if (enc(t ? &tmB2 : &tmB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, kp.ks[axis][which], dims,
             strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -922,22 +889,32 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
   if (!zz) tmB2 = tmB;
   // Shared memory (<= 225 KB): B resident when all its k-blocks fit next to 2 A stages;
   // otherwise 3 A stages (2 when needed) and as many streamed B stages as fit (at least 2).
-  const int budget = 225 * 1024 - 1024 - ks_tbytes(a) - ks_sbytes(a);
+  // Staged and row outputs take 12 epilogue warps (three column ranges) when that still
+  // leaves room for 2 A and 2 B stages, else 8.
   const int ab = ks_abytes(split), bb = ks_bbytes(split, a.Nc);
-  if (!zz && a.nkb * bb + 2 * ab <= budget) {
-    a.bres = 1;
-    a.AS = min(KS_MAXS, (budget - a.nkb * bb) / ab);
-    a.BS = 1;
-  } else {
-    a.bres = 0;
-    a.AS = 3;
-    a.BS = min(KS_MAXS, (budget - 3 * ab) / bb);
-    if (a.BS < 2) {
-      a.AS = 2;
-      a.BS = min(KS_MAXS, (budget - 2 * ab) / bb);
+  bool fits = false;
+  for (int parts = (ks_staged(a) || o.G == 1) ? 3 : 2; parts >= 2 && !fits; --parts) {
+    a.nparts = parts;
+    const int budget = 225 * 1024 - 1024 - ks_sbytes(a);
+    if (!zz && a.nkb * bb + 2 * ab <= budget) {
+      a.bres = 1;
+      a.AS = min(KS_MAXS, (budget - a.nkb * bb) / ab);
+      a.BS = 1;
+      fits = true;
+    } else {
+      a.bres = 0;
+      a.AS = 3;
+      a.BS = min(KS_MAXS, (budget - 3 * ab) / bb);
+      if (a.BS < 2) {
+        a.AS = 2;
+        a.BS = min(KS_MAXS, (budget - 2 * ab) / bb);
+      }
+      fits = a.BS >= 2;
     }
-    if (a.BS < 2) return cudaErrorNotSupported;
   }
+  if (!fits) return cudaErrorNotSupported;
+  // the second product's chunks (15 and 16 of 17) must fall in one part, the last
+  if (a.Nt && (a.nparts - 1) * (a.Nc / 16) / a.nparts > KS_NMAIN / 16) return cudaErrorNotSupported;
   const int smem = ks_smem(a);
   const int epi = ks_epi(a);
   auto kern = epi == EPI_T_STAGED ? k_dft_ks<EPI_T_STAGED>
