@@ -431,14 +431,14 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
             ptx::tc_fence_after();
             const uint32_t as = a0 + (uint32_t)(s * abytes), bs = b0 + (uint32_t)(sb * bbytes);
             const int nst = min(4, a.nk - kb * 4);
+            const uint64_t ah = desc_sw128(as), al = desc_sw128(as + (uint32_t)KS_ABOX);
+            const uint64_t bh = desc_sw128(bs), bl = desc_sw128(bs + blo);
             for (int j = 0; j < nst; ++j) {
-              const uint64_t dAh = desc_sw128(as + 32u * j), dBh = desc_sw128(bs + 32u * j);
-              ptx::mma_bf16(tmem, dAh, dBh, id, (kb | j) ? 1u : 0u);
+              const uint64_t o2 = 2u * (uint32_t)j;
+              ptx::mma_bf16(tmem, ah + o2, bh + o2, id, (kb | j) ? 1u : 0u);
               if (a.split) {
-                const uint64_t dAl = desc_sw128(as + (uint32_t)KS_ABOX + 32u * j);
-                const uint64_t dBl = desc_sw128(bs + blo + 32u * j);
-                ptx::mma_bf16(tmem, dAh, dBl, id, 1u);
-                ptx::mma_bf16(tmem, dAl, dBh, id, 1u);
+                ptx::mma_bf16(tmem, ah + o2, bl + o2, id, 1u);
+                ptx::mma_bf16(tmem, al + o2, bh + o2, id, 1u);
               }
             }
             ptx::mma_commit(ptx::smem_u32(&b_aempty[s]));
@@ -457,14 +457,14 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
             ptx::tc_fence_after();
             const uint32_t bs = b0 + (uint32_t)(sb * bbytes);
             const int nst = min(4, a.nk - kb * 4);
+            const uint64_t bh = desc_sw128(bs), bl = desc_sw128(bs + blo);
             for (int j = 0; j < nst; ++j) {
               const uint32_t ta = tmem + (uint32_t)(16 * (kb * 4 + j));   // hi at ta, lo at ta + 8
-              const uint64_t dBh = desc_sw128(bs + 32u * j);
-              ptx::mma_bf16_ta(d2, ta, dBh, id, (kb | j) ? 1u : 0u);
+              const uint64_t o2 = 2u * (uint32_t)j;
+              ptx::mma_bf16_ta(d2, ta, bh + o2, id, (kb | j) ? 1u : 0u);
               if (a.split) {
-                const uint64_t dBl = desc_sw128(bs + blo + 32u * j);
-                ptx::mma_bf16_ta(d2, ta, dBl, id, 1u);
-                ptx::mma_bf16_ta(d2, ta + 8u, dBh, id, 1u);
+                ptx::mma_bf16_ta(d2, ta, bl + o2, id, 1u);
+                ptx::mma_bf16_ta(d2, ta + 8u, bh + o2, id, 1u);
               }
             }
             ptx::mma_commit(ptx::smem_u32(&b_bempty[sb]));
@@ -495,33 +495,42 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
           ptx::tc_fence_after();
           const uint32_t as = a0 + (uint32_t)(s * abytes), bs = b0 + (uint32_t)(sb * bbytes);
           const int nst = min(4, a.nk - kb * 4);
+          // descriptors of the k-block's first 16-k step; a step advances the start address by
+          // 32 bytes, i.e. the descriptor by 2
+          const uint64_t ah = desc_sw128(as), al = desc_sw128(as + (uint32_t)KS_ABOX);
+          const uint64_t bh = desc_sw128(bs), bl = desc_sw128(bs + blo);
+          const uint64_t th = desc_sw128(bs + bto), tl = desc_sw128(bs + blo + bto);
+          // the columns 240..: the epilogue drains the previous tile's first, before this tile's
+          // second product starts; from then on the two products alternate step by step
+          const bool tail_wait = a.Nt && kb == 0 && i > 0;
           for (int j = 0; j < nst; ++j) {
-            const uint64_t dAh = desc_sw128(as + 32u * j), dBh = desc_sw128(bs + 32u * j);
-            ptx::mma_bf16(d, dAh, dBh, id, (kb | j) ? 1u : 0u);
+            const uint64_t o2 = 2u * (uint32_t)j;
+            const uint32_t acc = (kb | j) ? 1u : 0u;
+            ptx::mma_bf16(d, ah + o2, bh + o2, id, acc);
             if (a.split) {
-              const uint64_t dAl = desc_sw128(as + (uint32_t)KS_ABOX + 32u * j);
-              const uint64_t dBl = desc_sw128(bs + blo + 32u * j);
-              ptx::mma_bf16(d, dAh, dBl, id, 1u);
-              ptx::mma_bf16(d, dAl, dBh, id, 1u);
+              ptx::mma_bf16(d, ah + o2, bl + o2, id, 1u);
+              ptx::mma_bf16(d, al + o2, bh + o2, id, 1u);
+            }
+            if (a.Nt && !tail_wait) {
+              ptx::mma_bf16(dt, ah + o2, th + o2, idt, acc);
+              if (a.split) {
+                ptx::mma_bf16(dt, ah + o2, tl + o2, idt, 1u);
+                ptx::mma_bf16(dt, al + o2, th + o2, idt, 1u);
+              }
             }
           }
-          if (a.Nt) {
-            // the columns 240..: the epilogue drains the previous tile's first, before this
-            // tile's second product starts
-            if (kb == 0 && i > 0 &&
-                !ptx::mbar_wait_or_abort(ptx::smem_u32(&b_ttail), (uint32_t)(i - 1) & 1u, abort, a.poll)) {
+          if (tail_wait) {
+            if (!ptx::mbar_wait_or_abort(ptx::smem_u32(&b_ttail), (uint32_t)(i - 1) & 1u, abort, a.poll)) {
               ok = false;
               break;
             }
             ptx::tc_fence_after();
             for (int j = 0; j < nst; ++j) {
-              const uint64_t dAh = desc_sw128(as + 32u * j), dBh = desc_sw128(bs + bto + 32u * j);
-              ptx::mma_bf16(dt, dAh, dBh, idt, (kb | j) ? 1u : 0u);
+              const uint64_t o2 = 2u * (uint32_t)j;
+              ptx::mma_bf16(dt, ah + o2, th + o2, idt, j ? 1u : 0u);
               if (a.split) {
-                const uint64_t dAl = desc_sw128(as + (uint32_t)KS_ABOX + 32u * j);
-                const uint64_t dBl = desc_sw128(bs + blo + bto + 32u * j);
-                ptx::mma_bf16(dt, dAh, dBl, idt, 1u);
-                ptx::mma_bf16(dt, dAl, dBh, idt, 1u);
+                ptx::mma_bf16(dt, ah + o2, tl + o2, idt, 1u);
+                ptx::mma_bf16(dt, al + o2, th + o2, idt, 1u);
               }
             }
           }
