@@ -60,7 +60,10 @@ def _csrc_hash():
 def algorithmic(kernel, N, dims, kmode, T=10, peaks=None):
     X, Y, Z = dims
     B = {"flow_back_disp": 36, "flow_back_terms": 28, "fwd_residual": 36,
-         "fwd_flow": 36, "update": 36}
+         "fwd_flow": 36, "update": 36,
+         # residual b_j and map of step j + 1 over one read of u_j: u_j, I0, J1_j, W_j, v_j in;
+         # b_j (split), u_{j+1} out
+         "fwd_fused": 60}
     if kernel in B:
         return {"bound": "hbm", "bytes": B[kernel] * N}
     if kernel == "ereg":             # all T velocity fields read once: 12 B per voxel and step

@@ -28,7 +28,8 @@ struct Hook {
 
 enum KernelId {
   KID_BACK_DISP = 0, KID_BACK_TERMS, KID_FWD_TERMS, KID_FWD_FLOW, KID_KX_FWD, KID_KY_FWD,
-  KID_KZ_SYM, KID_KZ_INV, KID_KY_INV, KID_KX_INV, KID_UPDATE, KID_EREG, KID_KZ_FUSED, KID_COUNT
+  KID_KZ_SYM, KID_KZ_INV, KID_KY_INV, KID_KX_INV, KID_UPDATE, KID_EREG, KID_KZ_FUSED,
+  KID_FWD_FUSED, KID_COUNT
 };
 
 // ---- flows (kernels_flow.cu) ----
@@ -43,17 +44,20 @@ void launch_flow_back(const Grid& g, const void* vj, const float* u_next, float*
 // out[i] = (a[i], b[i]) as storage-type pairs.
 void launch_interleave(const void* a, const void* b, void* out, int64_t n, cudaStream_t s,
                        int st);
-// Forward sweep step j: b = c W_j (J0_j - J1_j) grad J0_j / h,  J0_j = I0 o (id + u_cur).
-// bsplit 0: b as 3 fp32 fields; 1 / 2: b split for the pre-split K (bf16 hi plane / hi and lo
-// planes, rows of pitch px).
-void launch_fwd_terms(const Grid& g, const float* u_cur, const void* I0, const float* J1j,
-                      const float* Wj, float* b, float c, float ihx, float ihy, float ihz,
-                      cudaStream_t s, int st, int bsplit = 0, int px = 0);
 // Forward sweep step j: u_next = -dt v_j / h + u_cur(x - dt v_j / h) (u_cur == nullptr: id);
 // if last, J0_T = I0 o (id + u_next) and E_data.
 void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u_next,
                      float dtx, float dty, float dtz, bool last, const void* I0, const void* I1,
                      const void* M, float* J0T, Acc* acc, cudaStream_t s, int st, int rk = 0);
+// Forward sweep step j in one pass over u_cur = phi_{j,0} - id (nullptr: id): the residual
+// b = c W_j (J0_j - J1_j) grad J0_j / h with J0_j = I0 o (id + u_cur) (bsplit 0: b as 3 fp32
+// fields; 1 / 2: b split for the pre-split K, bf16 hi plane / hi and lo planes, rows of pitch
+// px), and u_next as launch_fwd_flow (with J0_T and E_data when last).
+void launch_fwd_fused(const Grid& g, const void* vj, const float* u_cur, float* u_next,
+                      float dtx, float dty, float dtz, bool last, const void* I0, const float* J1j,
+                      const float* Wj, float* b, float c, float ihx, float ihy, float ihz,
+                      int bsplit, int px, const void* I1, const void* M, float* J0T, Acc* acc,
+                      cudaStream_t s, int st, int rk = 0);
 // E_reg of all T fields v[T][3][N] into acc->e_reg (unscaled sum of |(gamma - alpha Lap_h) v|^2).
 void launch_ereg(const Grid& g, const void* v, int T, float alpha, float gamma, float ihx2,
                  float ihy2, float ihz2, Acc* acc, cudaStream_t s, int st);

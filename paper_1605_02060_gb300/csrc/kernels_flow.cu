@@ -283,18 +283,16 @@ __device__ __forceinline__ float J0_at(const Grid& g, const float* __restrict__ 
                                    (float)z + __ldg(u + 2 * g.N + idx)));
 }
 
-// b as fp32 components (bsplit == 0), or split into bf16 hi/lo planes for the pre-split K
-// (bsplit 1: hi plane only, 2: hi and lo): element ((comp Z + z) Y + y) px + x of each plane,
-// planes 3 Z Y px elements apart.
-template <typename ST, int BSPLIT>
-__global__ void __launch_bounds__(256, 8) k_fwd_terms(Grid g, const float* __restrict__ uc,
-                                                      const ST* __restrict__ I0,
-                                                      const float* __restrict__ J1j,
-                                                      const float* __restrict__ Wj,
-                                                      float* __restrict__ b, float c, float ihx,
-                                                      float ihy, float ihz, int px) {
-  int x, y, z, idx;
-  if (!voxel3d(g, x, y, z, idx)) return;
+// b_j at voxel (x, y, z) = idx, as fp32 components (bsplit == 0), or split into bf16 hi/lo
+// planes for the pre-split K (bsplit 1: hi plane only, 2: hi and lo): element
+// ((comp Z + z) Y + y) px + x of each plane, planes 3 Z Y px elements apart.
+template <typename ST>
+__device__ __forceinline__ void fwd_terms_at(const Grid& g, const float* __restrict__ uc,
+                                             const ST* __restrict__ I0,
+                                             const float* __restrict__ J1j,
+                                             const float* __restrict__ Wj, float* __restrict__ b,
+                                             float c, float ihx, float ihy, float ihz, int bsplit,
+                                             int px, int x, int y, int z, int idx) {
   const float w = Wj[idx];
   float bx = 0.f, by = 0.f, bz = 0.f;
   if (w != 0.0f) {
@@ -331,7 +329,7 @@ __global__ void __launch_bounds__(256, 8) k_fwd_terms(Grid g, const float* __res
       bz = r * gr[2] * ihz;
     }
   }
-  if (BSPLIT) {
+  if (bsplit) {
     __nv_bfloat16* h = reinterpret_cast<__nv_bfloat16*>(b);
     const int64_t cs = (int64_t)g.nz * g.ny * px;
     const int64_t o = ((int64_t)z * g.ny + y) * px + x;
@@ -340,7 +338,7 @@ __global__ void __launch_bounds__(256, 8) k_fwd_terms(Grid g, const float* __res
     for (int e = 0; e < 3; ++e) {
       const __nv_bfloat16 hb = __float2bfloat16_rn(bc[e]);
       h[e * cs + o] = hb;
-      if (BSPLIT == 2) h[3 * cs + e * cs + o] = __float2bfloat16_rn(bc[e] - __bfloat162float(hb));
+      if (bsplit == 2) h[3 * cs + e * cs + o] = __float2bfloat16_rn(bc[e] - __bfloat162float(hb));
     }
   } else {
     b[idx] = bx;
@@ -349,22 +347,63 @@ __global__ void __launch_bounds__(256, 8) k_fwd_terms(Grid g, const float* __res
   }
 }
 
-void launch_fwd_terms(const Grid& g, const float* u_cur, const void* I0, const float* J1j,
-                      const float* Wj, float* b, float c, float ihx, float ihy, float ihz,
-                      cudaStream_t s, int st, int bsplit, int px) {
-#define FWD_TERMS(ST_, BS_)                                                                    \
-  k_fwd_terms<ST_, BS_><<<grid3d(g), kBlock3d, 0, s>>>(g, u_cur, (const ST_*)I0, J1j, Wj, b, c, \
-                                                       ihx, ihy, ihz, px)
-  if (st) {
-    if (bsplit == 2) FWD_TERMS(__nv_bfloat16, 2);
-    else if (bsplit == 1) FWD_TERMS(__nv_bfloat16, 1);
-    else FWD_TERMS(__nv_bfloat16, 0);
-  } else {
-    if (bsplit == 2) FWD_TERMS(float, 2);
-    else if (bsplit == 1) FWD_TERMS(float, 1);
-    else FWD_TERMS(float, 0);
+// Forward sweep, step j in one pass over u_j = phi_{j,0} - id: the residual b_j (as k_fwd_terms)
+// and the next map u_{j+1}(x) = -dt v_j(x)/h + u_j(x - dt v_j(x)/h) (as k_disp_march, s = -1;
+// uc == nullptr: u_j = 0).  LAST (j = T - 1) also gives J0_T = I0 o (id + u_T) and E_data, as
+// k_fwd_last_march.  A thread marches ZC planes in z; the velocity of plane z+1 is requested
+// before plane z's lookups, and the residual's lookups are independent of the map's.
+template <typename ST, int ZC, bool RK, bool LAST>
+__global__ void __launch_bounds__(256) k_fwd_fused_march(
+    Grid g, const ST* __restrict__ vj, const float* __restrict__ uc, float* __restrict__ un,
+    float dtx, float dty, float dtz, const ST* __restrict__ I0, const float* __restrict__ J1j,
+    const float* __restrict__ Wj, float* __restrict__ b, float c, float ihx, float ihy, float ihz,
+    int bsplit, int px, const ST* __restrict__ I1, const ST* __restrict__ M,
+    float* __restrict__ J0T, Acc* acc) {
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+  float edata = 0.f;
+  if (x < g.nx && y < g.ny) {
+    const int z0 = blockIdx.z * ZC, z1 = min(z0 + ZC, g.nz);
+    const int plane = g.nx * g.ny;
+    int idx = (z0 * g.ny + y) * g.nx + x;
+    float a0 = ldf(vj + idx), a1 = ldf(vj + g.N + idx), a2 = ldf(vj + 2 * g.N + idx);
+    for (int z = z0; z < z1; ++z, idx += plane) {
+      float n0 = 0.f, n1 = 0.f, n2 = 0.f;
+      if (z + 1 < z1) {
+        n0 = ldf_now(vj + idx + plane);
+        n1 = ldf_now(vj + g.N + idx + plane);
+        n2 = ldf_now(vj + 2 * g.N + idx + plane);
+      }
+      float dx, dy, dz;       // the step's displacement (voxels), backward in time
+      if (RK) {
+        rk4_disp(g, vj, (float)x, (float)y, (float)z, a0, a1, a2, -dtx, -dty, -dtz, dx, dy, dz);
+      } else {
+        dx = -(dtx * a0);
+        dy = -(dty * a1);
+        dz = -(dtz * a2);
+      }
+      float ox = dx, oy = dy, oz = dz;
+      if (uc) {
+        const Tri w = tri_setup(g, (float)x + dx, (float)y + dy, (float)z + dz);
+        ox += tri_apply(uc, w);
+        oy += tri_apply(uc + g.N, w);
+        oz += tri_apply(uc + 2 * g.N, w);
+      }
+      fwd_terms_at(g, uc, I0, J1j, Wj, b, c, ihx, ihy, ihz, bsplit, px, x, y, z, idx);
+      un[idx] = ox;
+      un[g.N + idx] = oy;
+      un[2 * g.N + idx] = oz;
+      if (LAST) {
+        const float j0 = tri_apply_t(I0, tri_setup(g, (float)x + ox, (float)y + oy, (float)z + oz));
+        J0T[idx] = j0;
+        const float r = j0 - ldf(I1 + idx);
+        edata = fmaf(ldf(M + idx) * r, r, edata);
+      }
+      a0 = n0;
+      a1 = n1;
+      a2 = n2;
+    }
   }
-#undef FWD_TERMS
+  if (LAST) block_sum_f_atomic(edata, &acc->e_data);
 }
 
 // Forward sweep, last step: u_T = -dt v_{T-1}/h + u_cur(x - dt v_{T-1}/h), then J0_T = I0 o
@@ -423,6 +462,26 @@ __global__ void __launch_bounds__(256) k_fwd_last_march(Grid g, const ST* __rest
     }
   }
   block_sum_f_atomic(edata, &acc->e_data);
+}
+
+void launch_fwd_fused(const Grid& g, const void* vj, const float* u_cur, float* u_next,
+                      float dtx, float dty, float dtz, bool last, const void* I0, const float* J1j,
+                      const float* Wj, float* b, float c, float ihx, float ihy, float ihz,
+                      int bsplit, int px, const void* I1, const void* M, float* J0T, Acc* acc,
+                      cudaStream_t s, int st, int rk) {
+  const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + kFlowZ - 1) / kFlowZ);
+#define FWD_FUSED(ST_, RK_, LAST_)                                                             \
+  k_fwd_fused_march<ST_, kFlowZ, RK_, LAST_><<<grid, kBlock3d, 0, s>>>(                       \
+      g, (const ST_*)vj, u_cur, u_next, dtx, dty, dtz, (const ST_*)I0, J1j, Wj, b, c, ihx, ihy, \
+      ihz, bsplit, px, (const ST_*)I1, (const ST_*)M, J0T, acc)
+  if (st) {
+    if (rk) { if (last) FWD_FUSED(__nv_bfloat16, true, true); else FWD_FUSED(__nv_bfloat16, true, false); }
+    else { if (last) FWD_FUSED(__nv_bfloat16, false, true); else FWD_FUSED(__nv_bfloat16, false, false); }
+  } else {
+    if (rk) { if (last) FWD_FUSED(float, true, true); else FWD_FUSED(float, true, false); }
+    else { if (last) FWD_FUSED(float, false, true); else FWD_FUSED(float, false, false); }
+  }
+#undef FWD_FUSED
 }
 
 void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u_next,

@@ -159,7 +159,7 @@ const char* kernel_name(int kid) {
   static const char* names[KID_COUNT] = {"flow_back_disp", "flow_back_terms", "fwd_residual",
                                          "fwd_flow", "K_x_fwd", "K_y_fwd", "K_z_symbol",
                                          "K_z_inv", "K_y_inv", "K_x_inv_update", "update", "ereg",
-                                         "K_z_fused"};
+                                         "K_z_fused", "fwd_fused"};
   return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 
@@ -381,15 +381,13 @@ int record_step(lddmm_ctx* ctx) {
   int pf = 0;
   for (int j = 0; j < T; ++j) {
     void* vj = vptr(ctx, j, N);
-    hk(KID_FWD_TERMS, 0);
-    launch_fwd_terms(g, uc, L.I0, ctx->J1 + j * N, ctx->W + j * N, ctx->b, c, 1.0f / L.hx,
-                     1.0f / L.hy, 1.0f / L.hz, s, ctx->st, bsplit, ks_pitch(g.nx));
-    hk(KID_FWD_TERMS, 1);
     float* unx = ctx->uF[pf];
-    hk(KID_FWD_FLOW, 0);
-    launch_fwd_flow(g, vj, uc, unx, dtx, dty, dtz, j == T - 1, L.I0, L.I1, L.M, ctx->J0T,
-                    ctx->acc, s, ctx->st, rk_of(ctx));
-    hk(KID_FWD_FLOW, 1);
+    // the residual b_j and the map of step j + 1 in one pass over u_j
+    hk(KID_FWD_FUSED, 0);
+    launch_fwd_fused(g, vj, uc, unx, dtx, dty, dtz, j == T - 1, L.I0, ctx->J1 + j * N,
+                     ctx->W + j * N, ctx->b, c, 1.0f / L.hx, 1.0f / L.hy, 1.0f / L.hz, bsplit,
+                     ks_pitch(g.nx), L.I1, L.M, ctx->J0T, ctx->acc, s, ctx->st, rk_of(ctx));
+    hk(KID_FWD_FUSED, 1);
     // K b_j and the update v_j <- v_j - eps (2 v_j - K b_j): fused into the last DFT pass (for
     // bf16 storage on the pre-split path too), else a separate pass
     if (ctx->st == 0) {
