@@ -222,8 +222,12 @@ cudaError_t conv_tc_fwd(const float* x, const void* w, const float* bias, float*
   int tcols = 32;
   while (tcols < Np) tcols <<= 1;
   const int smem = CV_STAGES * cv_stage_bytes(Np);
-  cudaError_t e = cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  static int limit = 0;   // only ever raised (a recorded launch may need more than this one)
+  if (smem > limit) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    limit = smem;
+  }
   const long long nv = (long long)n * n * n;
   dim3 grid((unsigned)((nv + 127) / 128), (unsigned)B);
   k_conv_tc<<<grid, CV_THREADS, smem, s>>>(x, (const __nv_bfloat16*)w, bias, y, Ci, Co, Np, n, ks,

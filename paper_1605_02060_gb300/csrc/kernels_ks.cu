@@ -50,6 +50,7 @@ constexpr int KS_MAXS = 6;                 // ring depths (A and streamed B) at 
 // two accumulators at TMEM columns 0 and 240) and a second product the columns 240.. (N = 32)
 // into one accumulator at TMEM column 480, which the epilogue drains first in every tile.
 constexpr int KS_NMAIN = 240, KS_TCOL = 480;
+constexpr int KS_SMEM_CAP = 225 * 1024;    // dynamic shared memory of any pass, at most
 
 struct KsArgs {
   int nlines;          // lines of the input field
@@ -904,7 +905,7 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
   bool fits = false;
   for (int parts = (ks_staged(a) || o.G == 1) ? 3 : 2; parts >= 2 && !fits; --parts) {
     a.nparts = parts;
-    const int budget = 225 * 1024 - 1024 - ks_sbytes(a);
+    const int budget = KS_SMEM_CAP - 1024 - ks_sbytes(a);
     if (!zz && a.nkb * bb + 2 * ab <= budget) {
       a.bres = 1;
       a.AS = min(KS_MAXS, (budget - a.nkb * bb) / ab);
@@ -931,8 +932,16 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
             : epi == EPI_ROWS     ? k_dft_ks<EPI_ROWS>
             : epi == EPI_ZZ       ? k_dft_ks<EPI_ZZ>
                                   : k_dft_ks<EPI_UPD>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  // The limit is set once per kernel, to the cap every pass stays under: a per-pass value would
+  // lower it below what an earlier launch of the same kernel (a recorded graph node) needs.
+  static bool limit_set[5] = {false, false, false, false, false};
+  if (smem > KS_SMEM_CAP) return cudaErrorNotSupported;
+  if (!limit_set[epi]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         KS_SMEM_CAP);
+    if (e != cudaSuccess) return e;
+    limit_set[epi] = true;
+  }
   if (!g_ks_sms) {
     int dev = 0;
     cudaGetDevice(&dev);

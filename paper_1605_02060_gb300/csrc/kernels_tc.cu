@@ -302,9 +302,15 @@ static int pow2_cols(int n) {
 template <int LOADT, int S>
 static cudaError_t launch_tc(const TcArgs& a, cudaStream_t s) {
   const int smem = S * stage_bytes(a.Npad);
-  cudaError_t e = cudaFuncSetAttribute(k_dft_tc<LOADT, S>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
+  // the kernel's shared-memory limit only ever rises: an earlier launch (a recorded graph node)
+  // may need more than this one
+  static int limit = 0;
+  if (smem > limit) {
+    cudaError_t e = cudaFuncSetAttribute(k_dft_tc<LOADT, S>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    limit = smem;
+  }
   const int grid = (a.M + TC_BM - 1) / TC_BM;
   if (grid > 0) k_dft_tc<LOADT, S><<<grid, TC_THREADS, smem, s>>>(a);
   return cudaGetLastError();
