@@ -34,10 +34,12 @@ enum KernelId {
 
 // ---- flows (kernels_flow.cu) ----
 // Velocity fields and images (vj, I0, I1, M) are stored as float (st = 0) or bf16 (st = 1);
-// displacements, J1, W, b and all arithmetic are float.
-// Backward sweep step j: u_cur = dt v_j / h + u_next(x + dt v_j / h)  (u_next == nullptr: id),
-// then J1_j = I1 o phi, W_j = (M o phi) det(I + Du_cur), min det into acc.  IM holds I1 and M
-// interleaved as pairs (launch_interleave).
+// displacements, J1, W, b and all arithmetic are float.  Maps (displacements) are planar,
+// [3][N], or, with quad = 1, [N] x (u_x, u_y, u_z, 0) (16 bytes a voxel): the iteration's sweeps
+// (launch_flow_back, launch_fwd_fused) and the maps they leave use the quad layout.
+// Backward sweep step j (quad maps): u_cur = dt v_j / h + u_next(x + dt v_j / h)
+// (u_next == nullptr: id), then J1_j = I1 o phi, W_j = (M o phi) det(I + Du_cur), min det into
+// acc.  IM holds I1 and M interleaved as pairs (launch_interleave).
 void launch_flow_back(const Grid& g, const void* vj, const float* u_next, float* u_cur,
                       const void* IM, float* J1j, float* Wj, float dtx, float dty, float dtz,
                       Acc* acc, cudaStream_t s, const Hook& hook, int st, int rk = 0);
@@ -48,8 +50,9 @@ void launch_interleave(const void* a, const void* b, void* out, int64_t n, cudaS
 // if last, J0_T = I0 o (id + u_next) and E_data.
 void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u_next,
                      float dtx, float dty, float dtz, bool last, const void* I0, const void* I1,
-                     const void* M, float* J0T, Acc* acc, cudaStream_t s, int st, int rk = 0);
-// Forward sweep step j in one pass over u_cur = phi_{j,0} - id (nullptr: id): the residual
+                     const void* M, float* J0T, Acc* acc, cudaStream_t s, int st, int rk = 0,
+                     int quad = 0);
+// Forward sweep step j (quad maps) in one pass over u_cur = phi_{j,0} - id (nullptr: id): the residual
 // b = c W_j (J0_j - J1_j) grad J0_j / h with J0_j = I0 o (id + u_cur) (bsplit 0: b as 3 fp32
 // fields; 1 / 2: b split for the pre-split K, bf16 hi plane / hi and lo planes, rows of pitch
 // px), and u_next as launch_fwd_flow (with J0_T and E_data when last).
@@ -66,9 +69,14 @@ void launch_update(const Grid& g, void* vj, const float* Kb, float eps, cudaStre
 // Displacement of phi_{1,0} / phi_{0,1} only (flows without the residual), to refresh maps.
 // rk = 1: RK4 along each step (v_j held over the step) instead of one lookup.
 void launch_flow_only_fwd(const Grid& g, const void* vj, const float* u_cur, float* u_next,
-                          float dtx, float dty, float dtz, cudaStream_t s, int st, int rk = 0);
+                          float dtx, float dty, float dtz, cudaStream_t s, int st, int rk = 0,
+                          int quad = 0);
 void launch_flow_only_back(const Grid& g, const void* vj, const float* u_next, float* u_cur,
-                           float dtx, float dty, float dtz, cudaStream_t s, int st, int rk = 0);
+                           float dtx, float dty, float dtz, cudaStream_t s, int st, int rk = 0,
+                           int quad = 0);
+// A map in the quad layout ([N] x (u_x, u_y, u_z, 0), the iteration's sweeps) to the planar one
+// ([3][N]).
+void launch_quad_to_planar(const float* quad, float* planar, int64_t n, cudaStream_t s);
 void launch_warp(const Grid& g, const float* src, const float* u, float* dst, cudaStream_t s);
 void launch_labels(const Grid& g, const uint16_t* L0, const float* u, uint16_t* dst,
                    cudaStream_t s);

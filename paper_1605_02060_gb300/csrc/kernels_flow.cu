@@ -35,6 +35,58 @@ static const dim3 kBlock3d(32, 8, 1);
 // costs two dependent memory latencies (v_j, then the eight corners at the displaced point); the
 // velocity of plane z+1 is loaded before the corners of plane z are requested, so the two
 // overlap.  Consecutive planes also gather from overlapping cells, which L1 keeps.
+// Maps (displacements u = phi - id, voxel units) in one of two layouts: planar, [3][N] (the
+// layout of the public entry points, the exact gradient and shooting), or quad, [N] x (u_x, u_y,
+// u_z, 0) in 16 bytes (the iteration's own sweeps: a stencil neighbour or a trilinear corner is
+// one 16-byte load instead of three).  Lookups interpolate each component in the same order
+// (x, then y, then z), so both layouts give the same values.
+template <bool Q> struct MapL;
+template <> struct MapL<false> {
+  static __device__ __forceinline__ float3 at(const float* __restrict__ u, int N, int i) {
+    return make_float3(__ldg(u + i), __ldg(u + N + i), __ldg(u + 2 * N + i));
+  }
+  static __device__ __forceinline__ void put(float* __restrict__ u, int N, int i, float a, float b,
+                                             float c) {
+    u[i] = a;
+    u[N + i] = b;
+    u[2 * N + i] = c;
+  }
+  static __device__ __forceinline__ float3 lerp(const float* __restrict__ u, int N, const Tri& w) {
+    return make_float3(tri_apply(u, w), tri_apply(u + N, w), tri_apply(u + 2 * N, w));
+  }
+};
+template <> struct MapL<true> {
+  static __device__ __forceinline__ float3 at(const float* __restrict__ u, int, int i) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(u) + i);
+    return make_float3(q.x, q.y, q.z);
+  }
+  static __device__ __forceinline__ void put(float* __restrict__ u, int, int i, float a, float b,
+                                             float c) {
+    reinterpret_cast<float4*>(u)[i] = make_float4(a, b, c, 0.f);
+  }
+  static __device__ __forceinline__ float lerp1(float c000, float c001, float c010, float c011,
+                                                float c100, float c101, float c110, float c111,
+                                                const Tri& w) {
+    const float a00 = c000 + w.tx * (c001 - c000);
+    const float a01 = c010 + w.tx * (c011 - c010);
+    const float a10 = c100 + w.tx * (c101 - c100);
+    const float a11 = c110 + w.tx * (c111 - c110);
+    const float b0 = a00 + w.ty * (a01 - a00);
+    const float b1 = a10 + w.ty * (a11 - a10);
+    return b0 + w.tz * (b1 - b0);
+  }
+  static __device__ __forceinline__ float3 lerp(const float* __restrict__ u, int, const Tri& w) {
+    const float4* p = reinterpret_cast<const float4*>(u) + w.base;
+    const float4 c000 = __ldg(p), c001 = __ldg(p + w.sx);
+    const float4 c010 = __ldg(p + w.sy), c011 = __ldg(p + w.sy + w.sx);
+    const float4 c100 = __ldg(p + w.sz), c101 = __ldg(p + w.sz + w.sx);
+    const float4 c110 = __ldg(p + w.sz + w.sy), c111 = __ldg(p + w.sz + w.sy + w.sx);
+    return make_float3(lerp1(c000.x, c001.x, c010.x, c011.x, c100.x, c101.x, c110.x, c111.x, w),
+                       lerp1(c000.y, c001.y, c010.y, c011.y, c100.y, c101.y, c110.y, c111.y, w),
+                       lerp1(c000.z, c001.z, c010.z, c011.z, c100.z, c101.z, c110.z, c111.z, w));
+  }
+};
+
 // RK4 displacement (voxels) of one time step of dy/dt = s v_j(y) / h from the grid point
 // (x, y, z), v_j held over the step (the paper's 4th-order Runge-Kutta, §2.4): k1 from the grid
 // value (a0, a1, a2), k2, k3, k4 from trilinear lookups of v_j at the stage points;
@@ -59,7 +111,7 @@ __device__ __forceinline__ void rk4_disp(const Grid& g, const ST* __restrict__ v
   d2 = (k1z + 2.f * k2z + 2.f * k3z + k4z) / 6.f;
 }
 
-template <typename ST, int SGN, int ZC, bool RK>
+template <typename ST, int SGN, int ZC, bool RK, bool Q>
 __global__ void __launch_bounds__(256) k_disp_march(Grid g, const ST* __restrict__ vj,
                                                     const float* __restrict__ uin,
                                                     float* __restrict__ uout, float dtx,
@@ -88,14 +140,12 @@ __global__ void __launch_bounds__(256) k_disp_march(Grid g, const ST* __restrict
     }
     float ox = dx, oy = dy, oz = dz;
     if (uin) {
-      const Tri w = tri_setup(g, (float)x + dx, (float)y + dy, (float)z + dz);
-      ox += tri_apply(uin, w);
-      oy += tri_apply(uin + g.N, w);
-      oz += tri_apply(uin + 2 * g.N, w);
+      const float3 r = MapL<Q>::lerp(uin, g.N, tri_setup(g, (float)x + dx, (float)y + dy, (float)z + dz));
+      ox += r.x;
+      oy += r.y;
+      oz += r.z;
     }
-    uout[idx] = ox;
-    uout[g.N + idx] = oy;
-    uout[2 * g.N + idx] = oz;
+    MapL<Q>::put(uout, g.N, idx, ox, oy, oz);
     a0 = n0;
     a1 = n1;
     a2 = n2;
@@ -106,27 +156,34 @@ __global__ void __launch_bounds__(256) k_disp_march(Grid g, const ST* __restrict
 // (ceil(nz/4) blocks along z) fills the GPU several times over.
 constexpr int kFlowZ = 4;
 
-template <typename ST, int SGN>
+template <typename ST, int SGN, bool Q>
 static void launch_disp_march(const Grid& g, const void* vj, const float* uin, float* uout,
                               float dtx, float dty, float dtz, cudaStream_t s, int rk) {
   const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + kFlowZ - 1) / kFlowZ);
   if (rk)
-    k_disp_march<ST, SGN, kFlowZ, true><<<grid, kBlock3d, 0, s>>>(g, (const ST*)vj, uin, uout,
-                                                                  dtx, dty, dtz);
+    k_disp_march<ST, SGN, kFlowZ, true, Q><<<grid, kBlock3d, 0, s>>>(g, (const ST*)vj, uin, uout,
+                                                                     dtx, dty, dtz);
   else
-    k_disp_march<ST, SGN, kFlowZ, false><<<grid, kBlock3d, 0, s>>>(g, (const ST*)vj, uin, uout,
-                                                                   dtx, dty, dtz);
+    k_disp_march<ST, SGN, kFlowZ, false, Q><<<grid, kBlock3d, 0, s>>>(g, (const ST*)vj, uin,
+                                                                      uout, dtx, dty, dtz);
+}
+
+template <bool Q>
+static void disp_step_l(int sgn, const Grid& g, const void* vj, const float* uin, float* uout,
+                        float dtx, float dty, float dtz, cudaStream_t s, int st, int rk) {
+  if (sgn > 0) {
+    if (st) launch_disp_march<__nv_bfloat16, 1, Q>(g, vj, uin, uout, dtx, dty, dtz, s, rk);
+    else launch_disp_march<float, 1, Q>(g, vj, uin, uout, dtx, dty, dtz, s, rk);
+  } else {
+    if (st) launch_disp_march<__nv_bfloat16, -1, Q>(g, vj, uin, uout, dtx, dty, dtz, s, rk);
+    else launch_disp_march<float, -1, Q>(g, vj, uin, uout, dtx, dty, dtz, s, rk);
+  }
 }
 
 static void disp_step(int sgn, const Grid& g, const void* vj, const float* uin, float* uout,
-                      float dtx, float dty, float dtz, cudaStream_t s, int st, int rk) {
-  if (sgn > 0) {
-    if (st) launch_disp_march<__nv_bfloat16, 1>(g, vj, uin, uout, dtx, dty, dtz, s, rk);
-    else launch_disp_march<float, 1>(g, vj, uin, uout, dtx, dty, dtz, s, rk);
-  } else {
-    if (st) launch_disp_march<__nv_bfloat16, -1>(g, vj, uin, uout, dtx, dty, dtz, s, rk);
-    else launch_disp_march<float, -1>(g, vj, uin, uout, dtx, dty, dtz, s, rk);
-  }
+                      float dtx, float dty, float dtz, cudaStream_t s, int st, int rk, int quad) {
+  if (quad) disp_step_l<true>(sgn, g, vj, uin, uout, dtx, dty, dtz, s, st, rk);
+  else disp_step_l<false>(sgn, g, vj, uin, uout, dtx, dty, dtz, s, st, rk);
 }
 
 // Backward sweep, part 2: J1_j = I1 o phi_{j,1}, W_j = (M o phi_{j,1}) det D phi_{j,1}.
@@ -167,7 +224,7 @@ __device__ __forceinline__ float2 tri_apply_pair(const PT* __restrict__ f, const
   return r;
 }
 
-template <typename ST, int ZC>
+template <typename ST, int ZC, bool Q>
 __global__ void __launch_bounds__(256) k_back_terms_march(Grid g, const float* __restrict__ uc,
                                                           const typename Pair<ST>::T* __restrict__ IM,
                                                           float* __restrict__ J1j,
@@ -184,8 +241,8 @@ __global__ void __launch_bounds__(256) k_back_terms_march(Grid g, const float* _
     const float ix = (x > 0 && x < g.nx - 1) ? 0.5f : 1.0f;
     const float iy = (y > 0 && y < g.ny - 1) ? 0.5f : 1.0f;
     auto ld3 = [&](int z, float* u) {
-      const int i = z * plane + rowoff + x;
-      u[0] = __ldg(uc + i); u[1] = __ldg(uc + g.N + i); u[2] = __ldg(uc + 2 * g.N + i);
+      const float3 r = MapL<Q>::at(uc, g.N, z * plane + rowoff + x);
+      u[0] = r.x; u[1] = r.y; u[2] = r.z;
     };
     float uP[3], uC[3], uN[3], uNN[3];
     ld3(z0 > 0 ? z0 - 1 : z0, uP);
@@ -197,16 +254,23 @@ __global__ void __launch_bounds__(256) k_back_terms_march(Grid g, const float* _
       if (z + 1 < z1) ld3(zn, uNN);
       const int i = z * plane + rowoff + x;
       float D[3][3];
-      const float* ucd[3] = {uc, uc + g.N, uc + 2 * g.N};
       const float iz = (z > 0 && z < g.nz - 1) ? 0.5f : 1.0f;
+      {
+        const int zp = z * plane;
+        const float3 xh = MapL<Q>::at(uc, g.N, zp + rowoff + xhi);
+        const float3 xl = MapL<Q>::at(uc, g.N, zp + rowoff + xlo);
+        const float3 yh = MapL<Q>::at(uc, g.N, zp + yhi * g.nx + x);
+        const float3 yl = MapL<Q>::at(uc, g.N, zp + ylo * g.nx + x);
+        const float xhv[3] = {xh.x, xh.y, xh.z}, xlv[3] = {xl.x, xl.y, xl.z};
+        const float yhv[3] = {yh.x, yh.y, yh.z}, ylv[3] = {yl.x, yl.y, yl.z};
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const float* q = ucd[d] + z * plane;
-        D[d][0] = (__ldg(q + rowoff + xhi) - __ldg(q + rowoff + xlo)) * ix;
-        D[d][1] = (__ldg(q + yhi * g.nx + x) - __ldg(q + ylo * g.nx + x)) * iy;
-        const float zh = z < g.nz - 1 ? uN[d] : uC[d], zl = z > 0 ? uP[d] : uC[d];
-        D[d][2] = (zh - zl) * iz;
-        D[d][d] += 1.0f;
+        for (int d = 0; d < 3; ++d) {
+          D[d][0] = (xhv[d] - xlv[d]) * ix;
+          D[d][1] = (yhv[d] - ylv[d]) * iy;
+          const float zh = z < g.nz - 1 ? uN[d] : uC[d], zl = z > 0 ? uP[d] : uC[d];
+          D[d][2] = (zh - zl) * iz;
+          D[d][d] += 1.0f;
+        }
       }
       const float det = D[0][0] * (D[1][1] * D[2][2] - D[1][2] * D[2][1]) -
                         D[0][1] * (D[1][0] * D[2][2] - D[1][2] * D[2][0]) +
@@ -254,39 +318,40 @@ void launch_flow_back(const Grid& g, const void* vj, const float* u_next, float*
                       const void* IM, float* J1j, float* Wj, float dtx, float dty, float dtz,
                       Acc* acc, cudaStream_t s, const Hook& hook, int st, int rk) {
   hook(KID_BACK_DISP, 0);
-  disp_step(+1, g, vj, u_next, u_cur, dtx, dty, dtz, s, st, rk);
+  disp_step(+1, g, vj, u_next, u_cur, dtx, dty, dtz, s, st, rk, 1);
   hook(KID_BACK_DISP, 1);
   hook(KID_BACK_TERMS, 0);
   const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + kFlowZ - 1) / kFlowZ);
   if (st)
-    k_back_terms_march<__nv_bfloat16, kFlowZ><<<grid, kBlock3d, 0, s>>>(
+    k_back_terms_march<__nv_bfloat16, kFlowZ, true><<<grid, kBlock3d, 0, s>>>(
         g, u_cur, (const __nv_bfloat162*)IM, J1j, Wj, acc);
   else
-    k_back_terms_march<float, kFlowZ><<<grid, kBlock3d, 0, s>>>(g, u_cur, (const float2*)IM, J1j,
-                                                                Wj, acc);
+    k_back_terms_march<float, kFlowZ, true><<<grid, kBlock3d, 0, s>>>(g, u_cur, (const float2*)IM,
+                                                                      J1j, Wj, acc);
   hook(KID_BACK_TERMS, 1);
 }
 
 void launch_flow_only_back(const Grid& g, const void* vj, const float* u_next, float* u_cur,
-                           float dtx, float dty, float dtz, cudaStream_t s, int st, int rk) {
-  disp_step(+1, g, vj, u_next, u_cur, dtx, dty, dtz, s, st, rk);
+                           float dtx, float dty, float dtz, cudaStream_t s, int st, int rk,
+                           int quad) {
+  disp_step(+1, g, vj, u_next, u_cur, dtx, dty, dtz, s, st, rk, quad);
 }
 
 // --------------------------------------------------------------------------------------------
 // Forward sweep, residual: b_j = c W_j (J0_j - J1_j) grad J0_j / h.
 // grad J0_j needs J0_j at the stencil neighbours; each is one trilinear lookup of I0 at the
 // neighbour's own mapped position (phi_{j,0} is known at every grid point).
-template <typename ST>
+template <bool Q, typename ST>
 __device__ __forceinline__ float J0_at(const Grid& g, const float* __restrict__ u,
                                        const ST* __restrict__ I0, int idx, int x, int y, int z) {
-  return tri_apply_t(I0, tri_setup(g, (float)x + __ldg(u + idx), (float)y + __ldg(u + g.N + idx),
-                                   (float)z + __ldg(u + 2 * g.N + idx)));
+  const float3 d = MapL<Q>::at(u, g.N, idx);
+  return tri_apply_t(I0, tri_setup(g, (float)x + d.x, (float)y + d.y, (float)z + d.z));
 }
 
 // b_j at voxel (x, y, z) = idx, as fp32 components (bsplit == 0), or split into bf16 hi/lo
 // planes for the pre-split K (bsplit 1: hi plane only, 2: hi and lo): element
 // ((comp Z + z) Y + y) px + x of each plane, planes 3 Z Y px elements apart.
-template <typename ST>
+template <bool Q, typename ST>
 __device__ __forceinline__ void fwd_terms_at(const Grid& g, const float* __restrict__ uc,
                                              const ST* __restrict__ I0,
                                              const float* __restrict__ J1j,
@@ -297,7 +362,7 @@ __device__ __forceinline__ void fwd_terms_at(const Grid& g, const float* __restr
   float bx = 0.f, by = 0.f, bz = 0.f;
   if (w != 0.0f) {
     float j0;
-    if (uc) j0 = J0_at(g, uc, I0, idx, x, y, z);
+    if (uc) j0 = J0_at<Q>(g, uc, I0, idx, x, y, z);
     else j0 = ldf(I0 + idx);
     const float r = c * w * (j0 - J1j[idx]);
     if (r != 0.0f) {
@@ -316,8 +381,8 @@ __device__ __forceinline__ void fwd_terms_at(const Grid& g, const float* __restr
         ph[e] += dh;
         pl[e] += dl;
         if (uc) {
-          fh = (dh == 0) ? j0 : J0_at(g, uc, I0, idx + hi, ph[0], ph[1], ph[2]);
-          fl = (dl == 0) ? j0 : J0_at(g, uc, I0, idx + lo, pl[0], pl[1], pl[2]);
+          fh = (dh == 0) ? j0 : J0_at<Q>(g, uc, I0, idx + hi, ph[0], ph[1], ph[2]);
+          fl = (dl == 0) ? j0 : J0_at<Q>(g, uc, I0, idx + lo, pl[0], pl[1], pl[2]);
         } else {
           fh = ldf(I0 + idx + hi);
           fl = ldf(I0 + idx + lo);
@@ -383,15 +448,14 @@ __global__ void __launch_bounds__(256) k_fwd_fused_march(
       }
       float ox = dx, oy = dy, oz = dz;
       if (uc) {
-        const Tri w = tri_setup(g, (float)x + dx, (float)y + dy, (float)z + dz);
-        ox += tri_apply(uc, w);
-        oy += tri_apply(uc + g.N, w);
-        oz += tri_apply(uc + 2 * g.N, w);
+        const float3 r =
+            MapL<true>::lerp(uc, g.N, tri_setup(g, (float)x + dx, (float)y + dy, (float)z + dz));
+        ox += r.x;
+        oy += r.y;
+        oz += r.z;
       }
-      fwd_terms_at(g, uc, I0, J1j, Wj, b, c, ihx, ihy, ihz, bsplit, px, x, y, z, idx);
-      un[idx] = ox;
-      un[g.N + idx] = oy;
-      un[2 * g.N + idx] = oz;
+      fwd_terms_at<true>(g, uc, I0, J1j, Wj, b, c, ihx, ihy, ihz, bsplit, px, x, y, z, idx);
+      MapL<true>::put(un, g.N, idx, ox, oy, oz);
       if (LAST) {
         const float j0 = tri_apply_t(I0, tri_setup(g, (float)x + ox, (float)y + oy, (float)z + oz));
         J0T[idx] = j0;
@@ -411,7 +475,7 @@ __global__ void __launch_bounds__(256) k_fwd_fused_march(
 // (the velocity of plane z+1 is loaded before plane z's lookups), so the three dependent
 // latencies of a voxel (v, the map at the displaced point, I0 at the mapped point) overlap with
 // the next plane's.
-template <typename ST, int ZC, bool RK>
+template <typename ST, int ZC, bool RK, bool Q>
 __global__ void __launch_bounds__(256) k_fwd_last_march(Grid g, const ST* __restrict__ vj,
                                                         const float* __restrict__ uc,
                                                         float* __restrict__ un, float dtx,
@@ -444,14 +508,13 @@ __global__ void __launch_bounds__(256) k_fwd_last_march(Grid g, const ST* __rest
       }
       float ox = dx, oy = dy, oz = dz;
       if (uc) {
-        const Tri w = tri_setup(g, (float)x + dx, (float)y + dy, (float)z + dz);
-        ox += tri_apply(uc, w);
-        oy += tri_apply(uc + g.N, w);
-        oz += tri_apply(uc + 2 * g.N, w);
+        const float3 r =
+            MapL<Q>::lerp(uc, g.N, tri_setup(g, (float)x + dx, (float)y + dy, (float)z + dz));
+        ox += r.x;
+        oy += r.y;
+        oz += r.z;
       }
-      un[idx] = ox;
-      un[g.N + idx] = oy;
-      un[2 * g.N + idx] = oz;
+      MapL<Q>::put(un, g.N, idx, ox, oy, oz);
       const float j0 = tri_apply_t(I0, tri_setup(g, (float)x + ox, (float)y + oy, (float)z + oz));
       J0T[idx] = j0;
       const float r = j0 - ldf(I1 + idx);
@@ -486,22 +549,23 @@ void launch_fwd_fused(const Grid& g, const void* vj, const float* u_cur, float* 
 
 void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u_next,
                      float dtx, float dty, float dtz, bool last, const void* I0, const void* I1,
-                     const void* M, float* J0T, Acc* acc, cudaStream_t s, int st, int rk) {
+                     const void* M, float* J0T, Acc* acc, cudaStream_t s, int st, int rk,
+                     int quad) {
   if (!last) {
-    disp_step(-1, g, vj, u_cur, u_next, dtx, dty, dtz, s, st, rk);
+    disp_step(-1, g, vj, u_cur, u_next, dtx, dty, dtz, s, st, rk, quad);
     return;
   }
   const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + kFlowZ - 1) / kFlowZ);
-#define FWD_LAST(ST_, RK_)                                                                    \
-  k_fwd_last_march<ST_, kFlowZ, RK_><<<grid, kBlock3d, 0, s>>>(                               \
+#define FWD_LAST(ST_, RK_, Q_)                                                                \
+  k_fwd_last_march<ST_, kFlowZ, RK_, Q_><<<grid, kBlock3d, 0, s>>>(                           \
       g, (const ST_*)vj, u_cur, u_next, dtx, dty, dtz, (const ST_*)I0, (const ST_*)I1,       \
       (const ST_*)M, J0T, acc)
-  if (st) {
-    if (rk) FWD_LAST(__nv_bfloat16, true);
-    else FWD_LAST(__nv_bfloat16, false);
+  if (quad) {
+    if (st) { if (rk) FWD_LAST(__nv_bfloat16, true, true); else FWD_LAST(__nv_bfloat16, false, true); }
+    else { if (rk) FWD_LAST(float, true, true); else FWD_LAST(float, false, true); }
   } else {
-    if (rk) FWD_LAST(float, true);
-    else FWD_LAST(float, false);
+    if (st) { if (rk) FWD_LAST(__nv_bfloat16, true, false); else FWD_LAST(__nv_bfloat16, false, false); }
+    else { if (rk) FWD_LAST(float, true, false); else FWD_LAST(float, false, false); }
   }
 #undef FWD_LAST
 }
@@ -653,8 +717,26 @@ void launch_ereg(const Grid& g, const void* v, int T, float alpha, float gamma, 
 }
 
 void launch_flow_only_fwd(const Grid& g, const void* vj, const float* u_cur, float* u_next,
-                          float dtx, float dty, float dtz, cudaStream_t s, int st, int rk) {
-  disp_step(-1, g, vj, u_cur, u_next, dtx, dty, dtz, s, st, rk);
+                          float dtx, float dty, float dtz, cudaStream_t s, int st, int rk,
+                          int quad) {
+  disp_step(-1, g, vj, u_cur, u_next, dtx, dty, dtz, s, st, rk, quad);
+}
+
+// quad map [N] x (x, y, z, 0) -> planar [3][N]
+__global__ void k_quad_to_planar(const float4* __restrict__ q, float* __restrict__ p, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float4 v = __ldg(q + i);
+    p[i] = v.x;
+    p[n + i] = v.y;
+    p[2 * n + i] = v.z;
+  }
+}
+
+void launch_quad_to_planar(const float* quad, float* planar, int64_t n, cudaStream_t s) {
+  if (n > 0)
+    k_quad_to_planar<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        reinterpret_cast<const float4*>(quad), planar, n);
 }
 
 // --------------------------------------------------------------------------------------------

@@ -479,7 +479,7 @@ int refresh_maps(lddmm_ctx* ctx, bool energy) {
   int pb = 0;
   for (int j = T - 1; j >= 0; --j) {
     float* uc = ctx->uB[pb];
-    launch_flow_only_back(g, vptr(ctx, j, N), un, uc, dtx, dty, dtz, s, ctx->st, rk_of(ctx));
+    launch_flow_only_back(g, vptr(ctx, j, N), un, uc, dtx, dty, dtz, s, ctx->st, rk_of(ctx), 1);
     un = uc;
     pb ^= 1;
   }
@@ -491,7 +491,7 @@ int refresh_maps(lddmm_ctx* ctx, bool energy) {
   for (int j = 0; j < T; ++j) {
     float* unx = ctx->uF[pf];
     launch_fwd_flow(g, vptr(ctx, j, N), uc, unx, dtx, dty, dtz, j == T - 1, L.I0, L.I1, L.M,
-                    ctx->J0T, ctx->acc, s, ctx->st, rk_of(ctx));
+                    ctx->J0T, ctx->acc, s, ctx->st, rk_of(ctx), 1);
     uc = unx;
     pf ^= 1;
   }
@@ -501,6 +501,13 @@ int refresh_maps(lddmm_ctx* ctx, bool energy) {
   ctx->j0_valid = true;
   (void)energy;
   return LDDMM_OK;
+}
+
+// The iteration leaves its maps in the quad layout; entry points that read a map (warps,
+// labels, landmarks) take a planar copy in the K work buffer, which is free between iterations.
+const float* planar_map(lddmm_ctx* ctx, const float* quad) {
+  launch_quad_to_planar(quad, ctx->work, ctx->levels[ctx->cur].g.N, ctx->stream);
+  return ctx->work;
 }
 
 int copy_out(lddmm_ctx* ctx, void* dst, const void* src, size_t bytes) {
@@ -652,8 +659,8 @@ int lddmm_create(const lddmm_params* p, const float* I0, const float* I1, const 
   }
   const int64_t ve = (T * 3 * N * (int64_t)ctx->es + 3) / 4;  // velocity storage, in floats
   ok = ok && A(dalloc(&ctx->v, ve)) && A(dalloc(&ctx->v_tmp, ve)) &&
-       A(dalloc(&ctx->uB[0], 3 * N)) && A(dalloc(&ctx->uB[1], 3 * N)) &&
-       A(dalloc(&ctx->uF[0], 3 * N)) && A(dalloc(&ctx->uF[1], 3 * N)) &&
+       A(dalloc(&ctx->uB[0], 4 * N)) && A(dalloc(&ctx->uB[1], 4 * N)) &&
+       A(dalloc(&ctx->uF[0], 4 * N)) && A(dalloc(&ctx->uF[1], 4 * N)) &&
        A(dalloc(&ctx->J1, T * N)) && A(dalloc(&ctx->W, T * N)) && A(dalloc(&ctx->b, ctx->kcap)) &&
        A(dalloc(&ctx->work, ctx->kcap)) && A(dalloc(&ctx->J0T, N)) && A(dalloc(&ctx->stage, 3 * N)) &&
        A(dalloc(&ctx->acc, 1)) && A(dalloc(&ctx->acc_init, 1)) && A(dalloc(&ctx->flag, 1)) &&
@@ -735,7 +742,7 @@ int lddmm_warp(lddmm_ctx* ctx, const float* src, float* dst, int direction) {
   if (rc) return rc;
   const bool dev = is_device_ptr(dst);
   float* d = dev ? dst : ctx->stage + g.N;
-  launch_warp(g, s, direction == 0 ? ctx->u10 : ctx->u01, d, ctx->stream);
+  launch_warp(g, s, planar_map(ctx, direction == 0 ? ctx->u10 : ctx->u01), d, ctx->stream);
   CK(cudaGetLastError());
   if (!dev) return copy_out(ctx, dst, d, g.N * sizeof(float));
   return LDDMM_OK;
@@ -754,7 +761,7 @@ int lddmm_transfer_labels(lddmm_ctx* ctx, const uint16_t* L0, uint16_t* dst) {
   }
   const bool dev = is_device_ptr(dst);
   uint16_t* d = dev ? dst : st + g.N;
-  launch_labels(g, s, ctx->u10, d, ctx->stream);
+  launch_labels(g, s, planar_map(ctx, ctx->u10), d, ctx->stream);
   CK(cudaGetLastError());
   if (!dev) return copy_out(ctx, dst, d, g.N * sizeof(uint16_t));
   return LDDMM_OK;
@@ -805,8 +812,15 @@ int lddmm_get_field(lddmm_ctx* ctx, int which, float* dst) {
     case LDDMM_FIELD_U01:
     case LDDMM_FIELD_J0:
       if (!ctx->maps_valid && (rc = refresh_maps(ctx, false))) return rc;
-      if (which == LDDMM_FIELD_U10) return copy_out(ctx, dst, ctx->u10, 3 * N * sizeof(float));
-      if (which == LDDMM_FIELD_U01) return copy_out(ctx, dst, ctx->u01, 3 * N * sizeof(float));
+      if (which == LDDMM_FIELD_U10 || which == LDDMM_FIELD_U01) {
+        const float* u = which == LDDMM_FIELD_U10 ? ctx->u10 : ctx->u01;
+        if (is_device_ptr(dst)) {
+          launch_quad_to_planar(u, dst, N, ctx->stream);
+          CK(cudaGetLastError());
+          return LDDMM_OK;
+        }
+        return copy_out(ctx, dst, planar_map(ctx, u), 3 * N * sizeof(float));
+      }
       return copy_out(ctx, dst, ctx->J0T, N * sizeof(float));
     case LDDMM_FIELD_I0:
     case LDDMM_FIELD_I1:
@@ -987,7 +1001,7 @@ int lddmm_landmark_error(lddmm_ctx* ctx, const float* xk, const float* yk, int n
   }
   cudaMemcpyAsync(pts, xk, (size_t)3 * n * sizeof(float), dx ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(pts + 3 * n, yk, (size_t)3 * n * sizeof(float), dy ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
-  landmark_errors(L.g, ctx->u01, pts, pts + 3 * n, n, L.hx, L.hy, L.hz, e, s);
+  landmark_errors(L.g, planar_map(ctx, ctx->u01), pts, pts + 3 * n, n, L.hx, L.hy, L.hz, e, s);
   cudaMemcpyAsync(err, e, (size_t)n * sizeof(double), de ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
   const cudaError_t le = cudaGetLastError();
   rc = wait_stream(ctx);
