@@ -35,8 +35,9 @@ enum KernelId {
 // ---- flows (kernels_flow.cu) ----
 // Velocity fields and images (vj, I0, I1, M) are stored as float (st = 0) or bf16 (st = 1);
 // displacements, J1, W, b and all arithmetic are float.  Maps (displacements) are planar,
-// [3][N], or, with quad = 1, [N] x (u_x, u_y, u_z, 0) (16 bytes a voxel): the iteration's sweeps
-// (launch_flow_back, launch_fwd_fused) and the maps they leave use the quad layout.
+// [3][N], or, with quad = 1, [N] x (u_x, u_y, u_z, 0) (16 bytes a voxel): the iteration's
+// backward sweep (launch_flow_back) and the map phi_{0,1} it leaves use the quad layout, the
+// forward sweep (launch_fwd_fused) and phi_{1,0} the planar one.
 // Backward sweep step j (quad maps): u_cur = dt v_j / h + u_next(x + dt v_j / h)
 // (u_next == nullptr: id), then J1_j = I1 o phi, W_j = (M o phi) det(I + Du_cur), min det into
 // acc.  IM holds I1 and M interleaved as pairs (launch_interleave).
@@ -52,7 +53,7 @@ void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u
                      float dtx, float dty, float dtz, bool last, const void* I0, const void* I1,
                      const void* M, float* J0T, Acc* acc, cudaStream_t s, int st, int rk = 0,
                      int quad = 0);
-// Forward sweep step j (quad maps) in one pass over u_cur = phi_{j,0} - id (nullptr: id): the residual
+// Forward sweep step j (planar maps) in one pass over u_cur = phi_{j,0} - id (nullptr: id): the residual
 // b = c W_j (J0_j - J1_j) grad J0_j / h with J0_j = I0 o (id + u_cur) (bsplit 0: b as 3 fp32
 // fields; 1 / 2: b split for the pre-split K, bf16 hi plane / hi and lo planes, rows of pitch
 // px), and u_next as launch_fwd_flow (with J0_T and E_data when last).

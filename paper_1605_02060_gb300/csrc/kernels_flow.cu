@@ -417,7 +417,7 @@ __device__ __forceinline__ void fwd_terms_at(const Grid& g, const float* __restr
 // uc == nullptr: u_j = 0).  LAST (j = T - 1) also gives J0_T = I0 o (id + u_T) and E_data, as
 // k_fwd_last_march.  A thread marches ZC planes in z; the velocity of plane z+1 is requested
 // before plane z's lookups, and the residual's lookups are independent of the map's.
-template <typename ST, int ZC, bool RK, bool LAST>
+template <typename ST, int ZC, bool RK, bool LAST, bool Q>
 __global__ void __launch_bounds__(256) k_fwd_fused_march(
     Grid g, const ST* __restrict__ vj, const float* __restrict__ uc, float* __restrict__ un,
     float dtx, float dty, float dtz, const ST* __restrict__ I0, const float* __restrict__ J1j,
@@ -449,13 +449,13 @@ __global__ void __launch_bounds__(256) k_fwd_fused_march(
       float ox = dx, oy = dy, oz = dz;
       if (uc) {
         const float3 r =
-            MapL<true>::lerp(uc, g.N, tri_setup(g, (float)x + dx, (float)y + dy, (float)z + dz));
+            MapL<Q>::lerp(uc, g.N, tri_setup(g, (float)x + dx, (float)y + dy, (float)z + dz));
         ox += r.x;
         oy += r.y;
         oz += r.z;
       }
-      fwd_terms_at<true>(g, uc, I0, J1j, Wj, b, c, ihx, ihy, ihz, bsplit, px, x, y, z, idx);
-      MapL<true>::put(un, g.N, idx, ox, oy, oz);
+      fwd_terms_at<Q>(g, uc, I0, J1j, Wj, b, c, ihx, ihy, ihz, bsplit, px, x, y, z, idx);
+      MapL<Q>::put(un, g.N, idx, ox, oy, oz);
       if (LAST) {
         const float j0 = tri_apply_t(I0, tri_setup(g, (float)x + ox, (float)y + oy, (float)z + oz));
         J0T[idx] = j0;
@@ -534,7 +534,7 @@ void launch_fwd_fused(const Grid& g, const void* vj, const float* u_cur, float* 
                       cudaStream_t s, int st, int rk) {
   const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + kFlowZ - 1) / kFlowZ);
 #define FWD_FUSED(ST_, RK_, LAST_)                                                             \
-  k_fwd_fused_march<ST_, kFlowZ, RK_, LAST_><<<grid, kBlock3d, 0, s>>>(                       \
+  k_fwd_fused_march<ST_, kFlowZ, RK_, LAST_, false><<<grid, kBlock3d, 0, s>>>(                \
       g, (const ST_*)vj, u_cur, u_next, dtx, dty, dtz, (const ST_*)I0, J1j, Wj, b, c, ihx, ihy, \
       ihz, bsplit, px, (const ST_*)I1, (const ST_*)M, J0T, acc)
   if (st) {

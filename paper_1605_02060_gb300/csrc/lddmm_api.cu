@@ -491,7 +491,7 @@ int refresh_maps(lddmm_ctx* ctx, bool energy) {
   for (int j = 0; j < T; ++j) {
     float* unx = ctx->uF[pf];
     launch_fwd_flow(g, vptr(ctx, j, N), uc, unx, dtx, dty, dtz, j == T - 1, L.I0, L.I1, L.M,
-                    ctx->J0T, ctx->acc, s, ctx->st, rk_of(ctx), 1);
+                    ctx->J0T, ctx->acc, s, ctx->st, rk_of(ctx), 0);
     uc = unx;
     pf ^= 1;
   }
@@ -503,8 +503,9 @@ int refresh_maps(lddmm_ctx* ctx, bool energy) {
   return LDDMM_OK;
 }
 
-// The iteration leaves its maps in the quad layout; entry points that read a map (warps,
-// labels, landmarks) take a planar copy in the K work buffer, which is free between iterations.
+// The iteration leaves phi_{0,1} in the quad layout (phi_{1,0} is planar); entry points that
+// read it (the inverse warp, landmarks, the map getter) take a planar copy in the K work buffer,
+// which is free between iterations.
 const float* planar_map(lddmm_ctx* ctx, const float* quad) {
   launch_quad_to_planar(quad, ctx->work, ctx->levels[ctx->cur].g.N, ctx->stream);
   return ctx->work;
@@ -742,7 +743,7 @@ int lddmm_warp(lddmm_ctx* ctx, const float* src, float* dst, int direction) {
   if (rc) return rc;
   const bool dev = is_device_ptr(dst);
   float* d = dev ? dst : ctx->stage + g.N;
-  launch_warp(g, s, planar_map(ctx, direction == 0 ? ctx->u10 : ctx->u01), d, ctx->stream);
+  launch_warp(g, s, direction == 0 ? ctx->u10 : planar_map(ctx, ctx->u01), d, ctx->stream);
   CK(cudaGetLastError());
   if (!dev) return copy_out(ctx, dst, d, g.N * sizeof(float));
   return LDDMM_OK;
@@ -761,7 +762,7 @@ int lddmm_transfer_labels(lddmm_ctx* ctx, const uint16_t* L0, uint16_t* dst) {
   }
   const bool dev = is_device_ptr(dst);
   uint16_t* d = dev ? dst : st + g.N;
-  launch_labels(g, s, planar_map(ctx, ctx->u10), d, ctx->stream);
+  launch_labels(g, s, ctx->u10, d, ctx->stream);
   CK(cudaGetLastError());
   if (!dev) return copy_out(ctx, dst, d, g.N * sizeof(uint16_t));
   return LDDMM_OK;
@@ -812,14 +813,14 @@ int lddmm_get_field(lddmm_ctx* ctx, int which, float* dst) {
     case LDDMM_FIELD_U01:
     case LDDMM_FIELD_J0:
       if (!ctx->maps_valid && (rc = refresh_maps(ctx, false))) return rc;
-      if (which == LDDMM_FIELD_U10 || which == LDDMM_FIELD_U01) {
-        const float* u = which == LDDMM_FIELD_U10 ? ctx->u10 : ctx->u01;
+      if (which == LDDMM_FIELD_U10) return copy_out(ctx, dst, ctx->u10, 3 * N * sizeof(float));
+      if (which == LDDMM_FIELD_U01) {
         if (is_device_ptr(dst)) {
-          launch_quad_to_planar(u, dst, N, ctx->stream);
+          launch_quad_to_planar(ctx->u01, dst, N, ctx->stream);
           CK(cudaGetLastError());
           return LDDMM_OK;
         }
-        return copy_out(ctx, dst, planar_map(ctx, u), 3 * N * sizeof(float));
+        return copy_out(ctx, dst, planar_map(ctx, ctx->u01), 3 * N * sizeof(float));
       }
       return copy_out(ctx, dst, ctx->J0T, N * sizeof(float));
     case LDDMM_FIELD_I0:
