@@ -63,7 +63,9 @@ def algorithmic(kernel, N, dims, kmode, T=10, peaks=None):
          "fwd_flow": 36, "update": 36,
          # residual b_j and map of step j + 1 over one read of u_j: u_j, I0, J1_j, W_j, v_j in;
          # b_j (split), u_{j+1} out
-         "fwd_fused": 60}
+         "fwd_fused": 60,
+         # J0_T = I0 o phi_{1,0} and E_data: u_T, I0, I1, M in; J0_T out
+         "fwd_J0T_Edata": 28}
     if kernel in B:
         return {"bound": "hbm", "bytes": B[kernel] * N}
     if kernel == "ereg":             # all T velocity fields read once: 12 B per voxel and step

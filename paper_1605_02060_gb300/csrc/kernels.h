@@ -29,7 +29,7 @@ struct Hook {
 enum KernelId {
   KID_BACK_DISP = 0, KID_BACK_TERMS, KID_FWD_TERMS, KID_FWD_FLOW, KID_KX_FWD, KID_KY_FWD,
   KID_KZ_SYM, KID_KZ_INV, KID_KY_INV, KID_KX_INV, KID_UPDATE, KID_EREG, KID_KZ_FUSED,
-  KID_FWD_FUSED, KID_COUNT
+  KID_FWD_FUSED, KID_J0_EDATA, KID_COUNT
 };
 
 // ---- flows (kernels_flow.cu) ----
@@ -56,12 +56,14 @@ void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u
 // Forward sweep step j (planar maps) in one pass over u_cur = phi_{j,0} - id (nullptr: id): the residual
 // b = c W_j (J0_j - J1_j) grad J0_j / h with J0_j = I0 o (id + u_cur) (bsplit 0: b as 3 fp32
 // fields; 1 / 2: b split for the pre-split K, bf16 hi plane / hi and lo planes, rows of pitch
-// px), and u_next as launch_fwd_flow (with J0_T and E_data when last).
+// px), and u_next as launch_fwd_flow (without J0_T and E_data: launch_j0_edata gives them).
 void launch_fwd_fused(const Grid& g, const void* vj, const float* u_cur, float* u_next,
-                      float dtx, float dty, float dtz, bool last, const void* I0, const float* J1j,
+                      float dtx, float dty, float dtz, const void* I0, const float* J1j,
                       const float* Wj, float* b, float c, float ihx, float ihy, float ihz,
-                      int bsplit, int px, const void* I1, const void* M, float* J0T, Acc* acc,
-                      cudaStream_t s, int st, int rk = 0);
+                      int bsplit, int px, cudaStream_t s, int st, int rk = 0);
+// J0_T = I0 o (id + u) and E_data = sum M (J0_T - I1)^2 into acc, from the planar map u = u_T.
+void launch_j0_edata(const Grid& g, const float* u, const void* I0, const void* I1,
+                     const void* M, float* J0T, Acc* acc, cudaStream_t s, int st);
 // E_reg of all T fields v[T][3][N] into acc->e_reg (unscaled sum of |(gamma - alpha Lap_h) v|^2).
 void launch_ereg(const Grid& g, const void* v, int T, float alpha, float gamma, float ihx2,
                  float ihy2, float ihz2, Acc* acc, cudaStream_t s, int st);

@@ -414,18 +414,17 @@ __device__ __forceinline__ void fwd_terms_at(const Grid& g, const float* __restr
 
 // Forward sweep, step j in one pass over u_j = phi_{j,0} - id: the residual b_j (as k_fwd_terms)
 // and the next map u_{j+1}(x) = -dt v_j(x)/h + u_j(x - dt v_j(x)/h) (as k_disp_march, s = -1;
-// uc == nullptr: u_j = 0).  LAST (j = T - 1) also gives J0_T = I0 o (id + u_T) and E_data, as
-// k_fwd_last_march.  A thread marches ZC planes in z; the velocity of plane z+1 is requested
-// before plane z's lookups, and the residual's lookups are independent of the map's.
-template <typename ST, int ZC, bool RK, bool LAST, bool Q>
+// uc == nullptr: u_j = 0).  A thread marches ZC planes in z; the velocity of plane z+1 is
+// requested before plane z's lookups, and the residual's lookups are independent of the map's.
+// J0_T and E_data of the last step come from u_T in a pass of their own (k_j0_edata_march):
+// folded in here they doubled this kernel's time for that step.
+template <typename ST, int ZC, bool RK, bool Q>
 __global__ void __launch_bounds__(256) k_fwd_fused_march(
     Grid g, const ST* __restrict__ vj, const float* __restrict__ uc, float* __restrict__ un,
     float dtx, float dty, float dtz, const ST* __restrict__ I0, const float* __restrict__ J1j,
     const float* __restrict__ Wj, float* __restrict__ b, float c, float ihx, float ihy, float ihz,
-    int bsplit, int px, const ST* __restrict__ I1, const ST* __restrict__ M,
-    float* __restrict__ J0T, Acc* acc) {
+    int bsplit, int px) {
   const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
-  float edata = 0.f;
   if (x < g.nx && y < g.ny) {
     const int z0 = blockIdx.z * ZC, z1 = min(z0 + ZC, g.nz);
     const int plane = g.nx * g.ny;
@@ -456,18 +455,39 @@ __global__ void __launch_bounds__(256) k_fwd_fused_march(
       }
       fwd_terms_at<Q>(g, uc, I0, J1j, Wj, b, c, ihx, ihy, ihz, bsplit, px, x, y, z, idx);
       MapL<Q>::put(un, g.N, idx, ox, oy, oz);
-      if (LAST) {
-        const float j0 = tri_apply_t(I0, tri_setup(g, (float)x + ox, (float)y + oy, (float)z + oz));
-        J0T[idx] = j0;
-        const float r = j0 - ldf(I1 + idx);
-        edata = fmaf(ldf(M + idx) * r, r, edata);
-      }
       a0 = n0;
       a1 = n1;
       a2 = n2;
     }
   }
-  if (LAST) block_sum_f_atomic(edata, &acc->e_data);
+}
+
+// J0_T = I0 o (id + u_T) and E_data = sum M (J0_T - I1)^2 from the final forward map u_T.
+// A thread marches ZC planes in z and requests plane z+1's map before plane z's lookup.
+template <typename ST, int ZC, bool Q>
+__global__ void __launch_bounds__(256) k_j0_edata_march(Grid g, const float* __restrict__ u,
+                                                        const ST* __restrict__ I0,
+                                                        const ST* __restrict__ I1,
+                                                        const ST* __restrict__ M,
+                                                        float* __restrict__ J0T, Acc* acc) {
+  const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+  float edata = 0.f;
+  if (x < g.nx && y < g.ny) {
+    const int z0 = blockIdx.z * ZC, z1 = min(z0 + ZC, g.nz);
+    const int plane = g.nx * g.ny;
+    int idx = (z0 * g.ny + y) * g.nx + x;
+    float3 d = MapL<Q>::at(u, g.N, idx);
+    for (int z = z0; z < z1; ++z, idx += plane) {
+      float3 dn = make_float3(0.f, 0.f, 0.f);
+      if (z + 1 < z1) dn = MapL<Q>::at(u, g.N, idx + plane);
+      const float j0 = tri_apply_t(I0, tri_setup(g, (float)x + d.x, (float)y + d.y, (float)z + d.z));
+      J0T[idx] = j0;
+      const float r = j0 - ldf(I1 + idx);
+      edata = fmaf(ldf(M + idx) * r, r, edata);
+      d = dn;
+    }
+  }
+  block_sum_f_atomic(edata, &acc->e_data);
 }
 
 // Forward sweep, last step: u_T = -dt v_{T-1}/h + u_cur(x - dt v_{T-1}/h), then J0_T = I0 o
@@ -528,23 +548,32 @@ __global__ void __launch_bounds__(256) k_fwd_last_march(Grid g, const ST* __rest
 }
 
 void launch_fwd_fused(const Grid& g, const void* vj, const float* u_cur, float* u_next,
-                      float dtx, float dty, float dtz, bool last, const void* I0, const float* J1j,
+                      float dtx, float dty, float dtz, const void* I0, const float* J1j,
                       const float* Wj, float* b, float c, float ihx, float ihy, float ihz,
-                      int bsplit, int px, const void* I1, const void* M, float* J0T, Acc* acc,
-                      cudaStream_t s, int st, int rk) {
+                      int bsplit, int px, cudaStream_t s, int st, int rk) {
   const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + kFlowZ - 1) / kFlowZ);
-#define FWD_FUSED(ST_, RK_, LAST_)                                                             \
-  k_fwd_fused_march<ST_, kFlowZ, RK_, LAST_, false><<<grid, kBlock3d, 0, s>>>(                \
+#define FWD_FUSED(ST_, RK_)                                                                    \
+  k_fwd_fused_march<ST_, kFlowZ, RK_, false><<<grid, kBlock3d, 0, s>>>(                       \
       g, (const ST_*)vj, u_cur, u_next, dtx, dty, dtz, (const ST_*)I0, J1j, Wj, b, c, ihx, ihy, \
-      ihz, bsplit, px, (const ST_*)I1, (const ST_*)M, J0T, acc)
+      ihz, bsplit, px)
   if (st) {
-    if (rk) { if (last) FWD_FUSED(__nv_bfloat16, true, true); else FWD_FUSED(__nv_bfloat16, true, false); }
-    else { if (last) FWD_FUSED(__nv_bfloat16, false, true); else FWD_FUSED(__nv_bfloat16, false, false); }
+    if (rk) FWD_FUSED(__nv_bfloat16, true); else FWD_FUSED(__nv_bfloat16, false);
   } else {
-    if (rk) { if (last) FWD_FUSED(float, true, true); else FWD_FUSED(float, true, false); }
-    else { if (last) FWD_FUSED(float, false, true); else FWD_FUSED(float, false, false); }
+    if (rk) FWD_FUSED(float, true); else FWD_FUSED(float, false);
   }
 #undef FWD_FUSED
+}
+
+void launch_j0_edata(const Grid& g, const float* u, const void* I0, const void* I1,
+                     const void* M, float* J0T, Acc* acc, cudaStream_t s, int st) {
+  const dim3 grid((g.nx + 31) / 32, (g.ny + 7) / 8, (g.nz + kFlowZ - 1) / kFlowZ);
+  if (st)
+    k_j0_edata_march<__nv_bfloat16, kFlowZ, false><<<grid, kBlock3d, 0, s>>>(
+        g, u, (const __nv_bfloat16*)I0, (const __nv_bfloat16*)I1, (const __nv_bfloat16*)M, J0T,
+        acc);
+  else
+    k_j0_edata_march<float, kFlowZ, false><<<grid, kBlock3d, 0, s>>>(
+        g, u, (const float*)I0, (const float*)I1, (const float*)M, J0T, acc);
 }
 
 void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u_next,

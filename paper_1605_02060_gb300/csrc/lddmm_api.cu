@@ -159,7 +159,7 @@ const char* kernel_name(int kid) {
   static const char* names[KID_COUNT] = {"flow_back_disp", "flow_back_terms", "fwd_residual",
                                          "fwd_flow", "K_x_fwd", "K_y_fwd", "K_z_symbol",
                                          "K_z_inv", "K_y_inv", "K_x_inv_update", "update", "ereg",
-                                         "K_z_fused", "fwd_fused"};
+                                         "K_z_fused", "fwd_fused", "fwd_J0T_Edata"};
   return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 
@@ -384,10 +384,15 @@ int record_step(lddmm_ctx* ctx) {
     float* unx = ctx->uF[pf];
     // the residual b_j and the map of step j + 1 in one pass over u_j
     hk(KID_FWD_FUSED, 0);
-    launch_fwd_fused(g, vj, uc, unx, dtx, dty, dtz, j == T - 1, L.I0, ctx->J1 + j * N,
-                     ctx->W + j * N, ctx->b, c, 1.0f / L.hx, 1.0f / L.hy, 1.0f / L.hz, bsplit,
-                     ks_pitch(g.nx), L.I1, L.M, ctx->J0T, ctx->acc, s, ctx->st, rk_of(ctx));
+    launch_fwd_fused(g, vj, uc, unx, dtx, dty, dtz, L.I0, ctx->J1 + j * N, ctx->W + j * N,
+                     ctx->b, c, 1.0f / L.hx, 1.0f / L.hy, 1.0f / L.hz, bsplit, ks_pitch(g.nx), s,
+                     ctx->st, rk_of(ctx));
     hk(KID_FWD_FUSED, 1);
+    if (j == T - 1) {     // J0_T = I0 o phi_{1,0} and E_data
+      hk(KID_J0_EDATA, 0);
+      launch_j0_edata(g, unx, L.I0, L.I1, L.M, ctx->J0T, ctx->acc, s, ctx->st);
+      hk(KID_J0_EDATA, 1);
+    }
     // K b_j and the update v_j <- v_j - eps (2 v_j - K b_j): fused into the last DFT pass (for
     // bf16 storage on the pre-split path too), else a separate pass
     if (ctx->st == 0) {
