@@ -224,8 +224,11 @@ __device__ __forceinline__ float2 tri_apply_pair(const PT* __restrict__ f, const
   return r;
 }
 
+// At most 40 registers (6 blocks of 256 threads per SM): the march waits on its lookups, and the
+// extra warps in flight outweigh the few spilled values (48 registers, 5 blocks: 93 against
+// 87 us at 264x160x228; 32 registers spill inside the loop and take 130 us).
 template <typename ST, int ZC, bool Q>
-__global__ void __launch_bounds__(256) k_back_terms_march(Grid g, const float* __restrict__ uc,
+__global__ void __launch_bounds__(256, 6) k_back_terms_march(Grid g, const float* __restrict__ uc,
                                                           const typename Pair<ST>::T* __restrict__ IM,
                                                           float* __restrict__ J1j,
                                                           float* __restrict__ Wj, Acc* acc) {
@@ -608,8 +611,9 @@ void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u
 // a row and takes the x-neighbours across vectors from the neighbouring lanes by shuffle (the
 // lanes at a warp or row edge load them).  Rows y+-1 are loaded (L1 hits: they are other
 // threads' centres).  The loads for plane z+1 are issued before plane z is evaluated.  The
-// stencil is ALU work (about 12 FP32 operations a voxel), so the vector width cuts the
-// per-voxel instruction count; a field is read once from DRAM.  Per-plane partial sums are
+// stencil is ALU work (eight FP32 operations a voxel in the form c0 u + cx (u_x- + u_x+) + ...),
+// and the kernel is bound by instruction issue more than by DRAM: the vector width and the
+// two-way unrolled march cut the per-voxel instruction count; a field is read once from DRAM.  Per-plane partial sums are
 // FP32, accumulated with compensated (Kahan) addition per thread; the block total goes to FP64.
 constexpr int kEregZ = 32;
 
@@ -653,11 +657,15 @@ __global__ void __launch_bounds__(256) k_ereg(Grid g, const ST* __restrict__ v, 
   const int ol = y * g.nx + xl, orr = y * g.nx + xr;
   const int nzc = (g.nz + kEregZ - 1) / kEregZ;
   const int64_t plane = (int64_t)g.nx * g.ny;
+  // (gamma - alpha Lap_h) u = c0 u + cx (u_x- + u_x+) + cy (u_y- + u_y+) + cz (u_z- + u_z+)
+  const float c0 = gamma + 2.f * alpha * (ihx2 + ihy2 + ihz2);
+  const float cx = -alpha * ihx2, cy = -alpha * ihy2, cz = -alpha * ihz2;
   float sum = 0.f, comp = 0.f;
   for (int q = blockIdx.y; q < nzc * nfield; q += gridDim.y) {
     const int f = q / nzc, z0 = (q - f * nzc) * kEregZ;
     const int z1 = min(z0 + kEregZ, g.nz);
     const ST* fb = v + (int64_t)f * g.N;
+    const ST* fe = fb + g.N;
     auto P = [&](int z) -> const ST* {
       z = z < 0 ? z + g.nz : (z >= g.nz ? z - g.nz : z);
       return fb + (int64_t)z * plane;
@@ -666,30 +674,37 @@ __global__ void __launch_bounds__(256) k_ereg(Grid g, const ST* __restrict__ v, 
     float hl = 0.f, hr = 0.f;
 #pragma unroll
     for (int k = 0; k < VEC; ++k) prv[k] = cur[k] = nxt[k] = am[k] = bp[k] = 0.f;
+    const ST* p1 = P(z0 + 1);     // plane z + 1 and plane z + 2, advanced with periodic wrap
+    const ST* p2 = P(z0 + 2);
     if (in) {
       ldvec<VEC>(P(z0 - 1) + oc, prv);
-      ldvec<VEC>(P(z0) + oc, cur);
-      ldvec<VEC>(P(z0 + 1) + oc, nxt);
       const ST* p0 = P(z0);
+      ldvec<VEC>(p0 + oc, cur);
+      ldvec<VEC>(p1 + oc, nxt);
       ldvec<VEC>(p0 + oym, am);
       ldvec<VEC>(p0 + oyp, bp);
       if (!lw) hl = ldf(p0 + ol);
       if (!rw) hr = ldf(p0 + orr);
     }
+    // unrolled by two, so the shift of the plane window costs no moves
+#pragma unroll 2
     for (int z = z0; z < z1; ++z) {
       // loads for the next plane: centre of z + 2, neighbours of z + 1
       float nn[VEC], am2[VEC], bp2[VEC];
       float hl2 = 0.f, hr2 = 0.f;
-#pragma unroll
-      for (int k = 0; k < VEC; ++k) nn[k] = am2[k] = bp2[k] = 0.f;
       if (in && z + 1 < z1) {
-        ldvec<VEC>(P(z + 2) + oc, nn);
-        const ST* p1 = P(z + 1);
+        ldvec<VEC>(p2 + oc, nn);
         ldvec<VEC>(p1 + oym, am2);
         ldvec<VEC>(p1 + oyp, bp2);
         if (!lw) hl2 = ldf(p1 + ol);
         if (!rw) hr2 = ldf(p1 + orr);
+      } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) nn[k] = am2[k] = bp2[k] = 0.f;
       }
+      p1 = p2;
+      p2 += plane;
+      if (p2 >= fe) p2 -= g.N;
       const float fromL = __shfl_up_sync(0xffffffffu, cur[VEC - 1], 1);
       const float fromR = __shfl_down_sync(0xffffffffu, cur[0], 1);
       if (in) {
@@ -698,10 +713,8 @@ __global__ void __launch_bounds__(256) k_ereg(Grid g, const ST* __restrict__ v, 
         for (int k = 0; k < VEC; ++k) {
           const float l = k > 0 ? cur[k - 1] : (lw ? fromL : hl);
           const float r = k + 1 < VEC ? cur[k + 1] : (rw ? fromR : hr);
-          const float c = cur[k];
-          const float lap = fmaf(-2.f, c, l + r) * ihx2 + fmaf(-2.f, c, am[k] + bp[k]) * ihy2 +
-                            fmaf(-2.f, c, prv[k] + nxt[k]) * ihz2;
-          const float Lv = fmaf(-alpha, lap, gamma * c);
+          const float Lv =
+              fmaf(cz, prv[k] + nxt[k], fmaf(cy, am[k] + bp[k], fmaf(cx, l + r, c0 * cur[k])));
           e = fmaf(Lv, Lv, e);
         }
         const float yk = e - comp;
