@@ -613,9 +613,10 @@ void launch_fwd_flow(const Grid& g, const void* vj, const float* u_cur, float* u
 // threads' centres).  The loads for plane z+1 are issued before plane z is evaluated.  The
 // stencil is ALU work (eight FP32 operations a voxel in the form c0 u + cx (u_x- + u_x+) + ...),
 // and the kernel is bound by instruction issue more than by DRAM: the vector width and the
-// two-way unrolled march cut the per-voxel instruction count; a field is read once from DRAM.  Per-plane partial sums are
-// FP32, accumulated with compensated (Kahan) addition per thread; the block total goes to FP64.
-constexpr int kEregZ = 32;
+// two-way unrolled march cut the per-voxel instruction count; a field is read once from DRAM.
+// Per-plane partial sums are FP32, accumulated with compensated (Kahan) addition per thread; the
+// block total goes to FP64.  64 planes per thread (268 -> 262 us against 32 at 264x160x228).
+constexpr int kEregZ = 64;
 
 template <int VEC>
 __device__ __forceinline__ void ldvec(const float* p, float (&o)[VEC]) {
