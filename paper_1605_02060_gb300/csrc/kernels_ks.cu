@@ -72,6 +72,7 @@ struct KsArgs {
   int* err;
   uint32_t poll;       // probes per pipeline wait before the CTA aborts
   int zz;              // the fused z pass: forward product, symbol, inverse product
+  int ostore;          // staged outputs leave by TMA stores of the warps' 32-line groups (tmO)
 };
 
 __host__ __device__ inline int ks_abytes(int split) { return (split ? 2 : 1) * KS_ABOX; }
@@ -287,6 +288,7 @@ template <int EPI>
 __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUtensorMap tmA,
                                                      const __grid_constant__ CUtensorMap tmB,
                                                      const __grid_constant__ CUtensorMap tmB2,
+                                                     const __grid_constant__ CUtensorMap tmO,
                                                      KsArgs a) {
   constexpr bool ZZ = EPI == EPI_ZZ;
   extern __shared__ __align__(1024) uint8_t smem_dyn[];
@@ -660,7 +662,43 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
       auto tcol = [&](int c) -> uint32_t {
         return tlane + (c < ntm ? tbuf + 16u * (uint32_t)c : (uint32_t)KS_TCOL + 16u * (uint32_t)(c - ntm));
       };
-      if constexpr (staged) {
+      if (staged && a.ostore) {
+        // Transposed split output by TMA: the output rows hold a multiple of 32 lines, so this
+        // warp's 32 lines (one TMEM lane quadrant) lie in one row.  Per 16-column chunk the warp
+        // writes its lines' hi and lo bf16 into its own 2 KB of the range's shared tile,
+        // [plane][16 columns][32 lines], and one lane stores them as two boxes of a 5-D tensor
+        // map over (line in row, row in block, column, block, plane).
+        uint16_t* wt = reinterpret_cast<uint16_t*>(stg) + part * (KS_CTILE / 2) + q * (2 * 16 * 32);
+        const uint32_t wts = ptx::smem_u32(wt);
+        const bool gvalid = line0 < a.nlines;
+        const long long t = line0 / o.E;
+        const int e0 = (int)(line0 - t * o.E), r1 = (int)(t % o.D), r3 = (int)(t / o.D);
+        for (int k = 0; k < cnt; ++k) {
+          const int c = chunk_at(k);
+          float vc[16];
+          ptx::tmem_ld16(tcol(c), vc);
+          if (k + 1 == ntl) {             // the second product's columns are read
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(ptx::smem_u32(&b_ttail));
+          }
+          if (lane == 0) ptx::bulk_wait_read_all();   // the previous boxes have left the tile
+          __syncwarp();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            uint16_t h, lo;
+            split1(vc[j], h, lo);
+            wt[j * 32 + lane] = h;
+            wt[512 + j * 32 + lane] = lo;
+          }
+          ptx::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0 && gvalid) {
+            ptx::tma_store_5d(&tmO, wts, e0, r1, c * 16, r3, 0);
+            if (a.split) ptx::tma_store_5d(&tmO, wts + 1024u, e0, r1, c * 16, r3, 1);
+            ptx::bulk_commit();
+          }
+        }
+      } else if constexpr (staged) {
         // Transposed split output.  Per 16-column chunk the four quadrant warps of this column
         // range write their lines' hi/lo bf16 into the range's shared tile [plane][col][line];
         // then each of the 128 threads stores 16-byte pieces of 8 consecutive lines of one
@@ -760,6 +798,7 @@ __global__ void __launch_bounds__(KS_NT, 1) k_dft_ks(const __grid_constant__ CUt
       ptx::tc_fence_before();
       ptx::mbar_arrive(ptx::smem_u32(&b_tempty[ab]));
     }
+    if (a.ostore && lane == 0) ptx::bulk_wait_all();   // this warp's stores have completed
   }
 
   // ------------------------------------------------------------ teardown
@@ -897,6 +936,25 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
       return cudaErrorInvalidValue;
   }
   if (!zz) tmB2 = tmB;
+  // Staged outputs whose rows hold a multiple of 32 lines leave by TMA stores: a 5-D map over
+  // (line in row e < E, row in block < D, column < Lc, block, plane), element
+  // (t / D * F + t % D) * P + e + column * G (+ plane) for line t * E + e, boxes of 32 lines x 16
+  // columns.  Other outputs (or addresses the map cannot describe) take the per-thread stores.
+  CUtensorMap tmO = tmA;
+  a.ostore = 0;
+  if (ks_staged(a) && o.E % 32 == 0 && (reinterpret_cast<uintptr_t>(o.out) & 15) == 0 &&
+      o.P % 8 == 0 && o.G % 8 == 0 && (o.F * o.P) % 8 == 0 && (!split || o.plane % 8 == 0)) {
+    const long long rows = (nlines + o.E - 1) / o.E;
+    cuuint64_t dims[5] = {(cuuint64_t)o.E, (cuuint64_t)o.D, (cuuint64_t)min(a.L, a.Nc),
+                          (cuuint64_t)((rows + o.D - 1) / o.D), (cuuint64_t)(split ? 2 : 1)};
+    cuuint64_t strides[4] = {(cuuint64_t)o.P * 2, (cuuint64_t)o.G * 2, (cuuint64_t)(o.F * o.P) * 2,
+                             (cuuint64_t)(split ? o.plane : o.F * o.P) * 2};
+    cuuint32_t box[5] = {32, 1, 16, 1, 1}, es[5] = {1, 1, 1, 1, 1};
+    if (enc(&tmO, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, o.out, dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+      a.ostore = 1;
+  }
   // Shared memory (<= 225 KB): B resident when all its k-blocks fit next to 2 A stages;
   // otherwise 3 A stages (2 when needed) and as many streamed B stages as fit (at least 2).
   // Staged and row outputs take 12 epilogue warps (three column ranges) when that still
@@ -949,7 +1007,7 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
     if (g_ks_sms <= 0) g_ks_sms = 148;
   }
   const int grid = a.ntiles < g_ks_sms ? a.ntiles : g_ks_sms;
-  if (grid > 0) kern<<<grid, KS_NT, smem, s>>>(tmA, tmB, tmB2, a);
+  if (grid > 0) kern<<<grid, KS_NT, smem, s>>>(tmA, tmB, tmB2, tmO, a);
   return cudaGetLastError();
 }
 
