@@ -415,7 +415,7 @@ __device__ __forceinline__ void fwd_terms_at(const Grid& g, const float* __restr
   }
 }
 
-// Forward sweep, step j in one pass over u_j = phi_{j,0} - id: the residual b_j (as k_fwd_terms)
+// Forward sweep, step j in one pass over u_j = phi_{j,0} - id: the residual b_j (fwd_terms_at)
 // and the next map u_{j+1}(x) = -dt v_j(x)/h + u_j(x - dt v_j(x)/h) (as k_disp_march, s = -1;
 // uc == nullptr: u_j = 0).  A thread marches ZC planes in z; the velocity of plane z+1 is
 // requested before plane z's lookups, and the residual's lookups are independent of the map's.
