@@ -939,10 +939,12 @@ cudaError_t ks_axis_pass(const KPlan& kp, int axis, bool inverse, int split, con
   // Staged outputs whose rows hold a multiple of 32 lines leave by TMA stores: a 5-D map over
   // (line in row e < E, row in block < D, column < Lc, block, plane), element
   // (t / D * F + t % D) * P + e + column * G (+ plane) for line t * E + e, boxes of 32 lines x 16
-  // columns.  Other outputs (or addresses the map cannot describe) take the per-thread stores.
+  // columns; the lines fill whole blocks of D rows, so every box lies inside the output.  Other
+  // outputs (or addresses the map cannot describe) take the per-thread stores.
   CUtensorMap tmO = tmA;
   a.ostore = 0;
-  if (ks_staged(a) && o.E % 32 == 0 && (reinterpret_cast<uintptr_t>(o.out) & 15) == 0 &&
+  if (ks_staged(a) && o.E % 32 == 0 && nlines % (o.E * o.D) == 0 &&
+      (reinterpret_cast<uintptr_t>(o.out) & 15) == 0 &&
       o.P % 8 == 0 && o.G % 8 == 0 && (o.F * o.P) % 8 == 0 && (!split || o.plane % 8 == 0)) {
     const long long rows = (nlines + o.E - 1) / o.E;
     cuuint64_t dims[5] = {(cuuint64_t)o.E, (cuuint64_t)o.D, (cuuint64_t)min(a.L, a.Nc),
