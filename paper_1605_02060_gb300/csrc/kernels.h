@@ -89,7 +89,8 @@ void launch_upsample(const Grid& coarse, const Grid& fine, float ratio, const vo
                      void* dst, int nfields, cudaStream_t s, int st);
 void launch_to_storage(const float* src, void* dst, int64_t n, cudaStream_t s, int st);
 void launch_from_storage(const void* src, float* dst, int64_t n, cudaStream_t s, int st);
-void launch_check_finite(const float* a, int64_t n, int* flag, cudaStream_t s);
+// *flag |= bit when a[0..n) holds a NaN or an infinity.
+void launch_check_finite(const float* a, int64_t n, int* flag, cudaStream_t s, int bit = 1);
 void launch_fill(float* a, int64_t n, float value, cudaStream_t s);
 void launch_dice_hist(const uint16_t* A, const uint16_t* B, int64_t n,
                       unsigned long long* hist /* 3 x 65536 */, cudaStream_t s);

@@ -941,17 +941,17 @@ void launch_from_storage(const void* src, float* dst, int64_t n, cudaStream_t s,
 }
 
 // --------------------------------------------------------------------------------------------
-__global__ void k_check_finite(const float* __restrict__ a, int64_t n, int* flag) {
+__global__ void k_check_finite(const float* __restrict__ a, int64_t n, int* flag, int bit) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int bad = 0;
   for (; i < n; i += stride) bad |= !isfinite(a[i]);
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, bit);
 }
 
-void launch_check_finite(const float* a, int64_t n, int* flag, cudaStream_t s) {
+void launch_check_finite(const float* a, int64_t n, int* flag, cudaStream_t s, int bit) {
   if (n <= 0) return;
-  k_check_finite<<<152 * 8, 256, 0, s>>>(a, n, flag);
+  k_check_finite<<<152 * 8, 256, 0, s>>>(a, n, flag, bit);
 }
 
 __global__ void k_fill(float* a, int64_t n, float value) {

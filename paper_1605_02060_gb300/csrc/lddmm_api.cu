@@ -248,10 +248,17 @@ int load_images(lddmm_ctx* ctx, const float* I0, const float* I1, const float* M
   if (M) CK(cudaMemcpyAsync(s2, M, N * sizeof(float), cudaMemcpyDefault, ctx->stream));
   else launch_fill(s2, N, 1.0f, ctx->stream);
   CK(cudaGetLastError());
-  int rc;
-  if ((rc = check_finite(ctx, s0, N, "I0"))) return rc;
-  if ((rc = check_finite(ctx, s1, N, "I1"))) return rc;
-  if ((rc = check_finite(ctx, s2, N, "M"))) return rc;
+  // the three images checked with one wait: bit 1 I0, bit 2 I1, bit 4 M
+  CK(cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->stream));
+  launch_check_finite(s0, N, ctx->flag, ctx->stream, 1);
+  launch_check_finite(s1, N, ctx->flag, ctx->stream, 2);
+  launch_check_finite(s2, N, ctx->flag, ctx->stream, 4);
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = wait_stream(ctx);
+  if (rc) return rc;
+  if (h) return fail(ctx, LDDMM_ERR_NONFINITE, std::string((h & 1) ? "I0" : (h & 2) ? "I1" : "M") +
+                                                   " holds NaN or Inf");
   launch_to_storage(s0, F.I0, N, ctx->stream, ctx->st);
   launch_to_storage(s1, F.I1, N, ctx->stream, ctx->st);
   launch_to_storage(s2, F.M, N, ctx->stream, ctx->st);
